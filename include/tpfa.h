@@ -1,0 +1,185 @@
+/*
+ * tpfa.h -- C ABI of the GB300 (sm_103a) TPFA assembly library.
+ *
+ * The library assembles, on one GPU, the residual and the Jacobian of the
+ * backward-Euler finite-volume discretisation of single-phase compressible
+ * Darcy flow on a structured nx x ny x nz grid (arXiv 2304.11274, Section 3):
+ *
+ *   R_K = V (phi(p_K) rho(p_K) - phi(pn_K) rho(pn_K)) / dt + sum_{L in adj(K)} F_KL   (Eq. vk)
+ *   F_KL = Upsilon_KL * lambda_up * dPhi_KL                                           (Eq. flux-calc)
+ *   dPhi_KL = (p_K - p_L) - rho_avg g (z_K - z_L),  rho_avg = (rho_K + rho_L) / 2
+ *   lambda_up = rho_K / mu if dPhi_KL > 0, else rho_L / mu                           (upwinding)
+ *   rho(p) = rho_ref exp(c_f (p - p_ref))                                            (Eq. density)
+ *   phi(p) = phi0 (1 + c_r (p - p_ref))
+ *   J_KL = dR_K / dp_L
+ *
+ * Conventions shared by every entry point:
+ *   - Cell (i, j, k) has linear index lin = i + nx (j + ny k): x fastest,
+ *     z slowest, the layout of Section 6.  z is the cell-centre DEPTH
+ *     (positive down), so F_KL is the mass outflow from K to L.  This is the
+ *     paper's Eq. flux-calc with K and L exchanged and z measured downward:
+ *     the form in which its upwind rule and the sign of Eq. vk agree.
+ *   - adj(K) is Section 5.1's neighbour set: (a) the four in-plane cardinal
+ *     cells, (b) the four in-plane diagonal cells when connectivity == 10,
+ *     (c) the cells above and below; cells outside the grid are not
+ *     neighbours (closed, no-flow boundary).
+ *   - Upsilon (the paper names it without a formula) is the two-point
+ *     harmonic form 2 k_K k_L / (k_K + k_L) * area / distance, with the
+ *     in-plane diagonal's distance sqrt(dx^2 + dy^2) and area
+ *     dz dx dy / sqrt(dx^2 + dy^2).
+ *   - Every pointer named *_dev is DEVICE memory on the current CUDA device,
+ *     owned by the caller unless stated otherwise.  `stream` is a
+ *     cudaStream_t passed as void* (NULL = the legacy default stream); every
+ *     call is asynchronous on it unless stated otherwise.
+ *   - Every call returns TPFA_OK (0) or a negative TPFA_ERR_* code and, on
+ *     error, sets a thread-local message read by tpfa_last_error_string().
+ *     Errors raised on the device (non-finite results) are latched in the
+ *     handle and returned by tpfa_sync_status().
+ *   - There is no host fallback: without a usable GPU every call that
+ *     computes returns TPFA_ERR_CUDA.
+ */
+#ifndef TPFA_H
+#define TPFA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPFA_OK 0
+#define TPFA_ERR_INVALID_ARG (-1) /* null handle/pointer, bad size, bad enum */
+#define TPFA_ERR_OOM (-2)         /* device allocation failed; nothing leaked */
+#define TPFA_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define TPFA_ERR_TOO_LARGE (-4)   /* N >= 2^31 cells, or a size beyond a stated limit */
+#define TPFA_ERR_NONFINITE (-5)   /* a residual or Jacobian value came out NaN/Inf */
+#define TPFA_ERR_NO_STATE (-6)    /* assemble called before tpfa_set_state */
+#define TPFA_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out */
+
+typedef struct tpfa_grid* tpfa_handle; /* opaque, library-owned */
+
+typedef enum {
+    TPFA_FP64 = 0,  /* every field, every operation and every output in FP64 */
+    TPFA_MIXED = 1  /* FP32 fields and flux arithmetic, FP32 Kahan residual sum,
+                       FP64 accumulation term and FP64 outputs R and diag64 */
+} tpfa_precision;
+
+/* Kernel variant used by the assemble calls (all give the same results up to
+ * the summation order stated for each). */
+typedef enum {
+    TPFA_KERNEL_AUTO = 0,  /* the tiled z-marching kernel */
+    TPFA_KERNEL_NAIVE = 1, /* one thread per cell, every neighbour read from
+                              global memory: the correctness baseline */
+    TPFA_KERNEL_TILED = 2  /* x-y tile in shared memory marching along z */
+} tpfa_kernel;
+
+typedef struct {
+    double rho_ref;   /* reference density rho_ref, kg/m^3 (Eq. density) */
+    double p_ref;     /* reference pressure p_ref, Pa (Eq. density) */
+    double c_f;       /* fluid compressibility c_f, 1/Pa (Eq. density) */
+    double mu;        /* viscosity mu, Pa s (> 0) */
+    double g;         /* gravitational acceleration g, m/s^2 */
+    double dt;        /* time step dt, s (> 0) (Eq. vk) */
+    double c_r;       /* rock compressibility c_r, 1/Pa; 0 = constant porosity */
+    double dx, dy, dz;/* cell size, m (> 0); V = dx dy dz */
+    int connectivity; /* 6 (faces) or 10 (faces + in-plane diagonals) */
+} tpfa_params;
+
+/*
+ * Create a grid (Section 3 problem statement; Section 6 layout).
+ *   out        : receives the handle.
+ *   nx, ny, nz : grid size, each >= 1, N = nx ny nz < 2^31 (else TOO_LARGE).
+ *   prm        : physical constants and connectivity (copied).
+ *   prec       : TPFA_FP64 or TPFA_MIXED.
+ *   perm_dev   : N doubles, permeability k (m^2, >= 0), read during the call only.
+ *   poro_dev   : N doubles, reference porosity phi0, read during the call only.
+ *   depth_dev  : N doubles, cell-centre depth z (m), read during the call only;
+ *                the mixed path stores it rounded to FP32.
+ * The library computes the owned transmissibilities (links to +x, +y, +z and,
+ * with 10-point connectivity, to (+x,+y) and (-x,+y)) in FP64 and stores them
+ * in the path's precision.  Synchronises `stream` before returning.
+ */
+int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params* prm,
+                     tpfa_precision prec, const double* perm_dev, const double* poro_dev,
+                     const double* depth_dev, void* stream);
+
+/*
+ * Bind the Newton state (Eq. vk): p^{n+1} (the iterate) and p^n (the previous
+ * time step).  p_dev and p_prev_dev hold N values of the handle's field type
+ * (double for TPFA_FP64, float for TPFA_MIXED); the pointers are BORROWED and
+ * must stay valid until the next set_state or destroy.  Computes
+ * m^n = (V/dt) phi(p^n) rho(p^n) in FP64 into library-owned memory, so call it
+ * again whenever p^n changes; when only p changes, tpfa_set_pressure is enough.
+ */
+int tpfa_set_state(tpfa_handle h, const void* p_dev, const void* p_prev_dev, void* stream);
+
+/* Rebind only the iterate p (same type and lifetime rules as set_state). */
+int tpfa_set_pressure(tpfa_handle h, const void* p_dev);
+
+/*
+ * Residual only (Algorithm 1 plus the accumulation term of Eq. vk).
+ *   R_dev : N doubles, written.
+ */
+int tpfa_assemble_residual(tpfa_handle h, double* R_dev, void* stream);
+
+/*
+ * Residual and Jacobian in one fused pass.
+ *   R_dev      : N doubles or NULL (then R is not written).
+ *   vals_dev   : nnz values in the CSR order of tpfa_get_pattern (columns
+ *                ascending within a row); double for TPFA_FP64, float for
+ *                TPFA_MIXED (its diagonal slot holds (float) J_KK).
+ *   diag64_dev : TPFA_MIXED: N doubles, the FP64 diagonal J_KK (may be NULL);
+ *                TPFA_FP64: must be NULL.
+ */
+int tpfa_assemble_jacobian(tpfa_handle h, double* R_dev, void* vals_dev, double* diag64_dev,
+                           void* stream);
+
+/* As tpfa_assemble_jacobian with an explicit kernel variant. */
+int tpfa_assemble_jacobian_kernel(tpfa_handle h, tpfa_kernel kern, double* R_dev, void* vals_dev,
+                                  double* diag64_dev, void* stream);
+
+/*
+ * End-to-end form with HOST buffers (pinned memory recommended): copies the
+ * N pressure values in p_host to a library-owned device buffer, binds it as
+ * the iterate, assembles, and copies R (N doubles), the CSR values (nnz) and,
+ * for TPFA_MIXED, diag64 (N doubles) back.  Any output pointer may be NULL.
+ * Requires a prior tpfa_set_state for p^n.  Synchronises `stream`.
+ */
+int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_host,
+                                void* vals_host, double* diag64_host, void* stream);
+
+/*
+ * The static Jacobian pattern: row_ptr (N+1 int64) and col_idx (nnz int32),
+ * columns ascending in each row.  Built on the first call (library-owned,
+ * read-only, freed by destroy); synchronises `stream` on that first call.
+ * Any out-pointer may be NULL.
+ */
+int tpfa_get_pattern(tpfa_handle h, const long long** row_ptr_dev, const int** col_idx_dev,
+                     long long* nnz, void* stream);
+
+/* Grid facts: sizes, nnz (closed form, no pattern build), precision. */
+int tpfa_grid_info(tpfa_handle h, int* nx, int* ny, int* nz, int* connectivity, long long* nnz,
+                   int* precision);
+
+/* Read the transmissibilities the library stores (for tests): `which` is
+ * 0 (+x), 1 (+y), 2 (+z), 3 (+x,+y), 4 (-x,+y); out_dev holds N values of the
+ * field type; links that leave the grid hold 0. */
+int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* stream);
+
+/*
+ * Wait for `stream`, then report and clear device-side errors latched since
+ * the last call: TPFA_ERR_NONFINITE if any assembled value was NaN/Inf.
+ */
+int tpfa_sync_status(tpfa_handle h, void* stream);
+
+/* Free everything the handle owns; NULL-safe.  Synchronises the device. */
+int tpfa_destroy(tpfa_handle h);
+
+/* Message of the last error on this host thread ("" if none). */
+const char* tpfa_last_error_string(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int tpfa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPFA_H */
