@@ -195,16 +195,20 @@ static orc_conn orc_connection(const orc_params* q, double T, double pK, double 
     return r;
 }
 
-/* Accumulation term of Eq. vk and its derivative for one cell. */
+/* Accumulation term of Eq. vk and its derivative for one cell.  The mass
+ * difference phi rho - phi^n rho^n is a difference of nearly equal numbers
+ * (relative size c_f |p - p^n|, about 1e-5 here), so FP64 would lose about
+ * eleven of its sixteen digits to cancellation; it is evaluated in long
+ * double (80-bit or 128-bit) and rounded to double once. */
 static void orc_accumulation(const orc_params* q, double phi0, double p, double pn,
                              double* A, double* dA) {
-    double V = q->dx * q->dy * q->dz;
-    double rho = orc_density(q, p);
-    double rhon = orc_density(q, pn);
-    double phi = orc_porosity(q, phi0, p);
-    double phin = orc_porosity(q, phi0, pn);
-    *A = V * (phi * rho - phin * rhon) / q->dt;
-    *dA = V * (phi0 * q->c_r * rho + phi * q->c_f * rho) / q->dt;
+    long double V = (long double)q->dx * q->dy * q->dz;
+    long double rho = q->rho_ref * expl((long double)q->c_f * ((long double)p - q->p_ref));
+    long double rhon = q->rho_ref * expl((long double)q->c_f * ((long double)pn - q->p_ref));
+    long double phi = phi0 * (1.0L + (long double)q->c_r * ((long double)p - q->p_ref));
+    long double phin = phi0 * (1.0L + (long double)q->c_r * ((long double)pn - q->p_ref));
+    *A = (double)(V * (phi * rho - phin * rhon) / q->dt);
+    *dA = (double)(V * (phi0 * q->c_r * rho + phi * q->c_f * rho) / q->dt);
 }
 
 /*
