@@ -1,0 +1,380 @@
+"""Benchmark: cells/s of the TPFA residual + Jacobian assembly on one GB300.
+
+Workload (default): the paper-shaped grid, 512 x 512 x 256 cells (67.1 M),
+10 links per cell (4 cardinal + 4 diagonal in-plane, 2 vertical), mixed
+precision (FP32 fields and flux arithmetic, FP32 Kahan residual, FP64
+accumulation term and FP64 residual/diagonal outputs), seeded synthetic
+inputs.  One step = one fused residual + Jacobian assembly over all cells
+with a new pressure vector (the repeated-application protocol of Section 3:
+"a different pressure vector at every call"); 8 distinct pressure vectors
+are cycled.  Inputs and outputs (~6.7 GB per step) exceed the 129 MB L2, so
+no flush is needed between steps.
+
+Multi-GPU (torchrun): every rank assembles its own replica grid (no
+collective on the data path); value = all ranks' cells / max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle (the test oracle, unmodified) on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cells/s for TPFA residual+Jacobian (1 GB300) and % of HBM roofline, mixed vs FP64"
+SHAPE = (512, 512, 256)
+CONN = 10
+WORKLOAD = "tpfa_residual_jacobian_512x512x256_10pt_mixed"
+KERNEL_SOURCES = ["tpfa_assemble.cu", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2304_11274_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "assemble_mixed_512x512x256.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.strip().startswith("- `"):
+                key, _, v = line.strip()[3:].partition("`:")
+                vals[key.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n, nnz, precision, crk=False):
+    """Bytes one assembly must move at least: each input field read once, each
+    output written once (halo re-reads excluded: they are cache traffic)."""
+    if precision == "mixed":
+        reads = n * (4 + 4 + 8 + 5 * 4 + 4 + (4 if crk else 0))  # p, p^n, m^n, 5 owned T, depth (+phi0)
+        writes = n * (8 + 8) + nnz * 4  # R, diag64, CSR values
+    else:
+        reads = n * (8 + 8 + 8 + 5 * 8 + 8 + (8 if crk else 0))
+        writes = n * 8 + nnz * 8
+    return reads + writes
+
+
+# ---------------------------------------------------------------------- our arm
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2304_11274_gb300 import build as libbuild
+    from paper_2304_11274_gb300 import synth
+    from paper_2304_11274_gb300.api import Grid
+
+    libbuild.build()
+    nx, ny, nz = SHAPE
+    prob = synth.make_problem(nx, ny, nz, synth.BASE_SEED + 1 + 100 * rank, connectivity=CONN)
+    pres = [prob.p] + synth.pressure_sequence(prob, 7, seed=synth.BASE_SEED + 11 + 100 * rank)
+    g = Grid(nx, ny, nz, prob.phys, "mixed", prob.perm, prob.poro, prob.depth, device=dev)
+    p_dev = [torch.as_tensor(x.astype(np.float32), device=dev) for x in pres]
+    pn_dev = torch.as_tensor(prob.pn.astype(np.float32), device=dev)
+    g.set_state(p_dev[0], pn_dev)
+    R, vals, diag = g.empty_outputs()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s):
+        g.set_pressure(p_dev[s % len(p_dev)])
+        g.assemble_jacobian(R, vals, diag)
+
+    for s in range(args.warmup):
+        step(s)
+    g.sync_status()
+    torch.cuda.synchronize(dev)
+
+    # per-launch CUDA events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        step(s)
+        ev[s][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    g.sync_status()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(ms.item())
+    ms_per_step = total_ms / args.steps
+    cells = prob.n * world
+    value = cells * args.steps / (total_ms * 1e-3)
+
+    # roofline of the assembly kernel (the only kernel in the step)
+    nbytes = algorithmic_bytes(prob.n, g.nnz, "mixed")
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    peak, peak_kind = measured_peaks()
+    achieved = nbytes / avg_launch_s / 1e9
+    khash = kernel_source_hash()
+    traffic = profiled_traffic(khash)
+
+    # end to end: host buffers through the C ABI (H2D of p, D2H of R, values, diag64)
+    import torch as _t
+    ph = [_t.as_tensor(x.astype(np.float32)).pin_memory() for x in pres[:2]]
+    Rh = _t.empty(prob.n, dtype=_t.float64).pin_memory()
+    vh = _t.empty(g.nnz, dtype=_t.float32).pin_memory()
+    dh = _t.empty(prob.n, dtype=_t.float64).pin_memory()
+    g.assemble_jacobian_host(ph[0], Rh, vh, dh)
+    e2e_steps = max(3, min(args.steps, 10))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter()
+    for s in range(e2e_steps):
+        g.assemble_jacobian_host(ph[s % 2], Rh, vh, dh)
+    e2e_s = time.perf_counter() - te
+    es = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(es, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = cells * e2e_steps / float(es.item())
+    h2d = prob.n * 4
+    d2h = prob.n * 8 + g.nnz * 4 + prob.n * 8
+
+    # the plain FP64 path on the same grid, for the mixed-vs-FP64 line
+    fp64 = None
+    if not args.skip_fp64:
+        del R, vals, diag
+        g.close()
+        g64 = Grid(nx, ny, nz, prob.phys, "fp64", prob.perm, prob.poro, prob.depth, device=dev)
+        p64 = [torch.as_tensor(x, device=dev) for x in pres[:2]]
+        g64.set_state(p64[0], torch.as_tensor(prob.pn, device=dev))
+        R64, v64, _ = g64.empty_outputs()
+        for s in range(2):
+            g64.set_pressure(p64[s % 2])
+            g64.assemble_jacobian(R64, v64, None)
+        torch.cuda.synchronize(dev)
+        nf = 5
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for s in range(nf):
+            g64.set_pressure(p64[s % 2])
+            g64.assemble_jacobian(R64, v64, None)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        g64.sync_status()
+        f_ms = a.elapsed_time(b) / nf
+        b64 = algorithmic_bytes(prob.n, g64.nnz, "fp64")
+        fp64 = {"value": prob.n / (f_ms * 1e-3), "unit": "cells/s", "ms_per_step": f_ms,
+                "hbm_GBps": b64 / (f_ms * 1e-3) / 1e9, "hbm_frac": b64 / (f_ms * 1e-3) / 1e9 / peak,
+                "note": "plain FP64 path, same grid; bound by the FP64 pipe, not HBM"}
+        g64.close()
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "cells/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded; log10 k ~ N(-13, 0.5), phi0 ~ U[0.1, 0.3], hydrostatic + U[-1e5, 1e5] Pa)",
+        "config": {"workload": WORKLOAD, "grid": list(SHAPE), "cells": prob.n, "links_per_cell": CONN,
+                   "nnz": g.nnz, "precision": "mixed: FP32 flux + Kahan residual, FP64 accumulation/diagonal/R",
+                   "l2": "inputs+outputs 6.7 GB per step > 129 MB L2; no flush",
+                   "pressure_vectors": len(pres), "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
+                     "kernel": "k_assemble_ymarch<float,DIAG,!CR,JAC>", "kernel_source_sha256_16": khash},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps, "api": "tpfa_assemble_jacobian_host (pinned host buffers)"},
+        "gpu_launches": args.steps,
+        "fp64": fp64,
+    }
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------- oracle on the host
+
+
+def cpu_sample_problem():
+    """A bounded slab of the same workload: 512 x 512 x 32 cells (8.4 M, one
+    eighth of the grid), same distributions and physics, FP32-rounded inputs."""
+    from paper_2304_11274_gb300 import synth
+    return synth.round_to_f32(synth.make_problem(512, 512, 32, synth.BASE_SEED + 1, connectivity=CONN))
+
+
+def cpu_baseline(budget_s=20.0):
+    import oracle
+    prob = cpu_sample_problem()
+    pat = oracle.pattern(prob.nx, prob.ny, prob.nz, CONN)
+    reps, t = 0, 0.0
+    while t < budget_s and reps < 50:
+        t0 = time.perf_counter()
+        oracle.assemble(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth, prob.p, prob.pn, pat=pat)
+        t += time.perf_counter() - t0
+        reps += 1
+    return {"value": prob.n * reps / t, "unit": "cells/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{prob.nx}x{prob.ny}x{prob.nz} slab of the same workload, {reps} assemblies, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    prob = cpu_sample_problem()
+    pat = oracle.pattern(prob.nx, prob.ny, prob.nz, CONN)
+    for _ in range(args.warmup):
+        oracle.assemble(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth, prob.p, prob.pn, pat=pat)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.assemble(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth, prob.p, prob.pn, pat=pat)
+    t = time.perf_counter() - t0
+    value = prob.n * args.steps / t
+    sample = f"{prob.nx}x{prob.ny}x{prob.nz} slab of the 512x512x256 workload per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)", "config": {"workload": WORKLOAD, "grid": list(SHAPE), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

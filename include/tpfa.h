@@ -62,13 +62,17 @@ typedef enum {
                        FP64 accumulation term and FP64 outputs R and diag64 */
 } tpfa_precision;
 
-/* Kernel variant used by the assemble calls (all give the same results up to
- * the summation order stated for each). */
+/* Kernel variant used by the assemble calls.  All variants evaluate every
+ * link and sum every row in the same order with the same roundings, so they
+ * give bit-identical results. */
 typedef enum {
-    TPFA_KERNEL_AUTO = 0,  /* the tiled z-marching kernel */
+    TPFA_KERNEL_AUTO = 0,  /* the library's choice (currently TILED) */
     TPFA_KERNEL_NAIVE = 1, /* one thread per cell, every neighbour read from
                               global memory: the correctness baseline */
-    TPFA_KERNEL_TILED = 2  /* x-y tile in shared memory marching along z */
+    TPFA_KERNEL_TILED = 2  /* a warp per 32-cell x-segment of a z-plane,
+                              marching along y with rows j-1, j, j+1 held in
+                              registers and x-neighbours exchanged by warp
+                              shuffles */
 } tpfa_kernel;
 
 typedef struct {
@@ -154,6 +158,18 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
  */
 int tpfa_get_pattern(tpfa_handle h, const long long** row_ptr_dev, const int** col_idx_dev,
                      long long* nnz, void* stream);
+
+/* Copy the pattern into caller-owned device buffers: row_ptr_out_dev (N+1
+ * int64) and col_idx_out_dev (nnz int32); either may be NULL.  Builds the
+ * library's copy first if needed (see tpfa_get_pattern).  Asynchronous on
+ * `stream` after that first build. */
+int tpfa_copy_pattern(tpfa_handle h, long long* row_ptr_out_dev, int* col_idx_out_dev, void* stream);
+
+/* Number of Jacobian entries of an nx x ny x nz grid with the given
+ * connectivity: N + 2 * (number of links), from the closed form of Section
+ * 5.1's neighbour sets.  Host-only, needs no GPU.  Returns a negative
+ * TPFA_ERR_* code for bad arguments. */
+long long tpfa_nnz(int nx, int ny, int nz, int connectivity);
 
 /* Grid facts: sizes, nnz (closed form, no pattern build), precision. */
 int tpfa_grid_info(tpfa_handle h, int* nx, int* ny, int* nz, int* connectivity, long long* nnz,

@@ -1,0 +1,162 @@
+"""PyTorch-facing wrapper of the TPFA C ABI (include/tpfa.h).
+
+PyTorch supplies device memory and streams; every step of the assembly runs
+in the library's CUDA kernels.  Tensors handed to ``set_state`` are borrowed
+by the library, so this wrapper keeps references to them.
+
+Physics follows arXiv 2304.11274, Section 3 (Eq. vk, Eq. flux-calc, Eq.
+density, Algorithm 1); see include/tpfa.h for the conventions.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _capi
+from ._capi import TPFA_FP64, TPFA_MIXED, TPFAError, check
+
+PRECISIONS = {"fp64": TPFA_FP64, "mixed": TPFA_MIXED}
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def params_struct(phys: dict) -> _capi.TPFAParams:
+    return _capi.TPFAParams(**{k: phys[k] for k, _ in _capi.TPFAParams._fields_})
+
+
+def _dev_f64(x, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device=device)
+
+
+class Grid:
+    """A structured grid with its rock properties resident on the GPU.
+
+    nx, ny, nz  : grid size (cell (i, j, k) is element i + nx (j + ny k))
+    phys        : dict of rho_ref, p_ref, c_f, mu, g, dt, c_r, dx, dy, dz, connectivity
+    precision   : "fp64" or "mixed"
+    perm, poro, depth : N values each (array-like or tensors), SI units
+    """
+
+    def __init__(self, nx, ny, nz, phys, precision, perm, poro, depth, device="cuda"):
+        self.lib = _capi.load()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.n = self.nx * self.ny * self.nz
+        self.phys = dict(phys)
+        self.precision = precision
+        self.device = torch.device(device)
+        self.dtype = torch.float32 if precision == "mixed" else torch.float64
+        prm = params_struct(self.phys)
+        with torch.cuda.device(self.device):
+            k = _dev_f64(perm, self.device)
+            ph = _dev_f64(poro, self.device)
+            z = _dev_f64(depth, self.device)
+            h = ctypes.c_void_p()
+            check(self.lib.tpfa_create_grid(ctypes.byref(h), self.nx, self.ny, self.nz, ctypes.byref(prm),
+                                            PRECISIONS[precision], _ptr(k), _ptr(ph), _ptr(z), _stream()))
+        self.handle = h
+        nnz = ctypes.c_longlong()
+        check(self.lib.tpfa_grid_info(h, None, None, None, None, ctypes.byref(nnz), None))
+        self.nnz = int(nnz.value)
+        self._p = None
+        self._pn = None
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.tpfa_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- state
+    def _field(self, x):
+        if isinstance(x, torch.Tensor) and x.device == self.device and x.dtype == self.dtype and x.is_contiguous():
+            t = x
+        else:
+            t = torch.as_tensor(np.asarray(x) if not isinstance(x, torch.Tensor) else x).to(
+                device=self.device, dtype=self.dtype).contiguous()
+        if t.numel() != self.n:
+            raise ValueError(f"expected {self.n} values, got {t.numel()}")
+        return t
+
+    def set_state(self, p, pn, stream=None):
+        """Bind p^{n+1} and p^n (computes m^n on the device)."""
+        p, pn = self._field(p), self._field(pn)
+        check(self.lib.tpfa_set_state(self.handle, _ptr(p), _ptr(pn), _stream(stream)))
+        self._p, self._pn = p, pn
+
+    def set_pressure(self, p):
+        p = self._field(p)
+        check(self.lib.tpfa_set_pressure(self.handle, _ptr(p)))
+        self._p = p
+
+    # -- outputs
+    def empty_outputs(self):
+        R = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        vals = torch.empty(self.nnz, dtype=self.dtype, device=self.device)
+        diag = torch.empty(self.n, dtype=torch.float64, device=self.device) if self.precision == "mixed" else None
+        return R, vals, diag
+
+    def assemble_residual(self, R=None, stream=None):
+        if R is None:
+            R = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        check(self.lib.tpfa_assemble_residual(self.handle, _ptr(R), _stream(stream)))
+        return R
+
+    def assemble_jacobian(self, R=None, vals=None, diag=None, kernel="auto", stream=None, want_residual=True):
+        """Fused residual + Jacobian.  Returns (R, vals, diag64); diag64 is
+        None on the FP64 path (the diagonal is in vals)."""
+        if vals is None:
+            R0, vals, diag0 = self.empty_outputs()
+            R = R0 if (R is None and want_residual) else R
+            diag = diag0 if diag is None else diag
+        check(self.lib.tpfa_assemble_jacobian_kernel(self.handle, _capi.KERNELS[kernel], _ptr(R), _ptr(vals),
+                                                     _ptr(diag), _stream(stream)))
+        return R, vals, diag
+
+    def assemble_jacobian_host(self, p_host: torch.Tensor, R_host=None, vals_host=None, diag_host=None, stream=None):
+        """End-to-end call with host buffers (pinned CPU tensors recommended)."""
+        if p_host.device.type != "cpu" or p_host.dtype != self.dtype or p_host.numel() != self.n:
+            raise ValueError("p_host must be a CPU tensor of the field dtype with N values")
+        check(self.lib.tpfa_assemble_jacobian_host(self.handle, _ptr(p_host), _ptr(R_host), _ptr(vals_host),
+                                                   _ptr(diag_host), _stream(stream)))
+        return R_host, vals_host, diag_host
+
+    def pattern(self, stream=None):
+        """(row_ptr int64[N+1], col_idx int32[nnz]) as device tensors."""
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        ci = torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        check(self.lib.tpfa_copy_pattern(self.handle, _ptr(rp), _ptr(ci), _stream(stream)))
+        return rp, ci
+
+    def transmissibility(self, which: int, stream=None):
+        out = torch.empty(self.n, dtype=self.dtype, device=self.device)
+        check(self.lib.tpfa_get_transmissibility(self.handle, int(which), _ptr(out), _stream(stream)))
+        return out
+
+    def sync_status(self, stream=None):
+        check(self.lib.tpfa_sync_status(self.handle, _stream(stream)))
+
+
+__all__ = ["Grid", "TPFAError", "PRECISIONS"]

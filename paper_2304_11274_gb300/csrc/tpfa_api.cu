@@ -1,0 +1,444 @@
+// tpfa_api.cu -- the C ABI declared in include/tpfa.h.
+//
+// Host logic only: argument checks, device memory of the handle, launches.
+// Every computation runs in the kernels of tpfa_setup.cu / tpfa_assemble.cu;
+// there is no host fallback.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "tpfa_common.cuh"
+#include "tpfa_impl.h"
+
+using namespace tpfa;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(TPFA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// TPFA_FAULT_INJECT=alloc makes every device allocation of the library fail,
+// so the out-of-memory path (error code, nothing leaked) can be tested
+// without exhausting a GPU.
+bool alloc_fault_injected() {
+    const char* v = getenv("TPFA_FAULT_INJECT");
+    return v != nullptr && strcmp(v, "alloc") == 0;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (alloc_fault_injected()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes > 0 ? bytes : 1);
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct tpfa_grid {
+    int device = 0;
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    tpfa_precision prec = TPFA_FP64;
+    tpfa_params prm{};
+    GridGeom geom{};
+    PhysF qf{};
+    PhysD qd{};
+    SetupPhys sp{};
+    bool crk = false;
+    size_t real_size = 8;
+    void* T[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // Tx, Ty, Tz, Tpp, Tmp
+    void* z = nullptr;
+    double* phi0_d = nullptr;
+    void* phi0_r = nullptr;  // phi0 in the field type (mixed path with c_r != 0)
+    double* mn = nullptr;
+    unsigned int* status = nullptr;
+    long long* row_ptr = nullptr;
+    int* col_idx = nullptr;
+    long long nnz = 0;
+    const void* p = nullptr;
+    const void* pn = nullptr;
+    bool has_state = false;
+    int JY = 32;
+    // buffers of the host-memory entry point, allocated on first use
+    void* h_p = nullptr;
+    double* h_R = nullptr;
+    void* h_vals = nullptr;
+    double* h_diag = nullptr;
+
+    void release() {
+        for (auto& t : T) dev_free(t), t = nullptr;
+        dev_free(z);
+        dev_free(phi0_d);
+        dev_free(phi0_r);
+        dev_free(mn);
+        dev_free(status);
+        dev_free(row_ptr);
+        dev_free(col_idx);
+        dev_free(h_p);
+        dev_free(h_R);
+        dev_free(h_vals);
+        dev_free(h_diag);
+        z = nullptr, phi0_d = nullptr, phi0_r = nullptr, mn = nullptr, status = nullptr;
+        row_ptr = nullptr, col_idx = nullptr, h_p = nullptr, h_R = nullptr, h_vals = nullptr, h_diag = nullptr;
+    }
+};
+
+namespace {
+
+bool finite_pos(double x) { return x > 0.0 && x < 1e300; }
+
+int check_params(const tpfa_params* prm) {
+    if (!prm) return fail(TPFA_ERR_INVALID_ARG, "params is NULL");
+    if (prm->connectivity != 6 && prm->connectivity != 10)
+        return fail(TPFA_ERR_INVALID_ARG, "connectivity must be 6 or 10 (got %d)", prm->connectivity);
+    if (!finite_pos(prm->mu)) return fail(TPFA_ERR_INVALID_ARG, "mu must be > 0");
+    if (!(prm->dt > 0.0)) return fail(TPFA_ERR_INVALID_ARG, "dt must be > 0");
+    if (!finite_pos(prm->dx) || !finite_pos(prm->dy) || !finite_pos(prm->dz))
+        return fail(TPFA_ERR_INVALID_ARG, "cell sizes must be > 0");
+    if (!(prm->rho_ref > 0.0)) return fail(TPFA_ERR_INVALID_ARG, "rho_ref must be > 0");
+    return TPFA_OK;
+}
+
+template <typename Real>
+AsmFields<Real> fields_of(const tpfa_grid* h) {
+    AsmFields<Real> f;
+    f.p = static_cast<const Real*>(h->p);
+    f.pn = static_cast<const Real*>(h->pn);
+    f.mn = h->mn;
+    f.z = static_cast<const Real*>(h->z);
+    f.phi0 = static_cast<const Real*>(h->phi0_r);
+    f.Tx = static_cast<const Real*>(h->T[0]);
+    f.Ty = static_cast<const Real*>(h->T[1]);
+    f.Tz = static_cast<const Real*>(h->T[2]);
+    f.Tpp = static_cast<const Real*>(h->T[3]);
+    f.Tmp = static_cast<const Real*>(h->T[4]);
+    return f;
+}
+
+int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st) {
+    cudaError_t e;
+    if (h->prec == TPFA_MIXED) {
+        AsmOut<float> o{R, static_cast<float*>(vals), diag64, h->status};
+        e = launch_assemble_mixed(kern, h->geom, h->qf, h->crk, fields_of<float>(h), o, h->JY, st);
+    } else {
+        AsmOut<double> o{R, static_cast<double*>(vals), nullptr, h->status};
+        e = launch_assemble_fp64(kern, h->geom, h->qd, h->crk, fields_of<double>(h), o, h->JY, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "assembly launch");
+    return TPFA_OK;
+}
+
+int check_handle(tpfa_handle h) {
+    if (!h) return fail(TPFA_ERR_INVALID_ARG, "handle is NULL");
+    return TPFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tpfa_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char* tpfa_last_error_string(void) { return g_err.c_str(); }
+
+int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params* prm, tpfa_precision prec,
+                     const double* perm_dev, const double* poro_dev, const double* depth_dev, void* stream) {
+    g_err.clear();
+    if (!out) return fail(TPFA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(TPFA_ERR_INVALID_ARG, "grid sizes must be >= 1 (%d %d %d)", nx, ny, nz);
+    const long long N = (long long)nx * ny * nz;
+    if (N >= (1LL << 31)) return fail(TPFA_ERR_TOO_LARGE, "N = %lld cells exceeds 2^31 - 1", N);
+    int rc = check_params(prm);
+    if (rc) return rc;
+    if (prec != TPFA_FP64 && prec != TPFA_MIXED) return fail(TPFA_ERR_INVALID_ARG, "bad precision %d", (int)prec);
+    if (!perm_dev || !poro_dev || !depth_dev) return fail(TPFA_ERR_INVALID_ARG, "perm/poro/depth must be non-NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    tpfa_grid* h = new tpfa_grid();
+    h->device = dev;
+    h->nx = nx, h->ny = ny, h->nz = nz, h->N = N;
+    h->prec = prec;
+    h->prm = *prm;
+    h->geom = GridGeom{nx, ny, nz, prm->connectivity == 10 ? 1 : 0};
+    h->crk = prm->c_r != 0.0;
+    h->real_size = prec == TPFA_MIXED ? sizeof(float) : sizeof(double);
+    const double V_dt = prm->dx * prm->dy * prm->dz / prm->dt;
+    h->qd = PhysD{prm->rho_ref, prm->p_ref, prm->c_f, 1.0 / prm->mu, prm->g, 0.5 * prm->g, V_dt, prm->c_r};
+    h->qf = PhysF{(float)prm->rho_ref, (float)prm->p_ref, (float)prm->c_f, (float)(1.0 / prm->mu),
+                  (float)prm->g, (float)(0.5 * prm->g), (float)V_dt, (float)prm->c_r};
+    h->sp = SetupPhys{prm->dx, prm->dy, prm->dz, prm->rho_ref, prm->p_ref, prm->c_f, prm->c_r, V_dt};
+    h->nnz = total_nnz(h->geom);
+
+    const size_t rb = h->real_size * (size_t)N;
+    const int nT = h->geom.diag ? 5 : 3;
+    bool ok = true;
+    for (int t = 0; t < nT && ok; ++t) ok = dev_alloc(&h->T[t], rb) == cudaSuccess;
+    ok = ok && dev_alloc(&h->z, rb) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&h->phi0_d, sizeof(double) * (size_t)N) == cudaSuccess;
+    if (ok && h->crk) ok = dev_alloc(&h->phi0_r, rb) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&h->mn, sizeof(double) * (size_t)N) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&h->status, sizeof(unsigned int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        h->release();
+        delete h;
+        return fail(TPFA_ERR_OOM, "device allocation failed for a %d x %d x %d grid", nx, ny, nz);
+    }
+    e = cudaMemsetAsync(h->status, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        if (prec == TPFA_MIXED)
+            e = launch_transmissibility_f32(h->geom, h->sp, perm_dev, (float*)h->T[0], (float*)h->T[1], (float*)h->T[2],
+                                            (float*)h->T[3], (float*)h->T[4], st);
+        else
+            e = launch_transmissibility_f64(h->geom, h->sp, perm_dev, (double*)h->T[0], (double*)h->T[1],
+                                            (double*)h->T[2], (double*)h->T[3], (double*)h->T[4], st);
+    }
+    if (e == cudaSuccess)
+        e = prec == TPFA_MIXED ? launch_convert_f32(depth_dev, (float*)h->z, N, st)
+                               : launch_copy_f64(depth_dev, (double*)h->z, N, st);
+    if (e == cudaSuccess) e = launch_copy_f64(poro_dev, h->phi0_d, N, st);
+    if (e == cudaSuccess && h->crk)
+        e = prec == TPFA_MIXED ? launch_convert_f32(poro_dev, (float*)h->phi0_r, N, st)
+                               : launch_copy_f64(poro_dev, (double*)h->phi0_r, N, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        h->release();
+        delete h;
+        return cuda_fail(e, "grid setup");
+    }
+    *out = h;
+    return TPFA_OK;
+}
+
+int tpfa_set_state(tpfa_handle h, const void* p_dev, const void* p_prev_dev, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!p_dev || !p_prev_dev) return fail(TPFA_ERR_INVALID_ARG, "p and p_prev must be non-NULL");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = h->prec == TPFA_MIXED
+                        ? launch_prev_mass_f32(h->sp, (const float*)p_prev_dev, h->phi0_d, h->mn, h->N, st)
+                        : launch_prev_mass_f64(h->sp, (const double*)p_prev_dev, h->phi0_d, h->mn, h->N, st);
+    if (e != cudaSuccess) return cuda_fail(e, "set_state launch");
+    h->p = p_dev;
+    h->pn = p_prev_dev;
+    h->has_state = true;
+    return TPFA_OK;
+}
+
+int tpfa_set_pressure(tpfa_handle h, const void* p_dev) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!p_dev) return fail(TPFA_ERR_INVALID_ARG, "p must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    h->p = p_dev;
+    return TPFA_OK;
+}
+
+int tpfa_assemble_residual(tpfa_handle h, double* R_dev, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!R_dev) return fail(TPFA_ERR_INVALID_ARG, "R must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    DeviceGuard dg(h->device);
+    return launch(h, AsmKernel::YMarch, R_dev, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int tpfa_assemble_jacobian_kernel(tpfa_handle h, tpfa_kernel kern, double* R_dev, void* vals_dev,
+                                  double* diag64_dev, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!vals_dev) return fail(TPFA_ERR_INVALID_ARG, "vals must be non-NULL");
+    if (h->prec == TPFA_FP64 && diag64_dev) return fail(TPFA_ERR_INVALID_ARG, "diag64 must be NULL on the FP64 path");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    AsmKernel k;
+    switch (kern) {
+        case TPFA_KERNEL_AUTO:
+        case TPFA_KERNEL_TILED: k = AsmKernel::YMarch; break;
+        case TPFA_KERNEL_NAIVE: k = AsmKernel::Naive; break;
+        default: return fail(TPFA_ERR_INVALID_ARG, "bad kernel variant %d", (int)kern);
+    }
+    DeviceGuard dg(h->device);
+    return launch(h, k, R_dev, vals_dev, diag64_dev, static_cast<cudaStream_t>(stream));
+}
+
+int tpfa_assemble_jacobian(tpfa_handle h, double* R_dev, void* vals_dev, double* diag64_dev, void* stream) {
+    return tpfa_assemble_jacobian_kernel(h, TPFA_KERNEL_AUTO, R_dev, vals_dev, diag64_dev, stream);
+}
+
+int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_host, void* vals_host,
+                                double* diag64_host, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!p_host) return fail(TPFA_ERR_INVALID_ARG, "p_host must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t pb = h->real_size * (size_t)h->N;
+    const size_t vb = h->real_size * (size_t)h->nnz;
+    bool ok = true;
+    if (!h->h_p) ok = dev_alloc(&h->h_p, pb) == cudaSuccess;
+    if (ok && !h->h_R) ok = dev_alloc((void**)&h->h_R, sizeof(double) * (size_t)h->N) == cudaSuccess;
+    if (ok && !h->h_vals) ok = dev_alloc(&h->h_vals, vb) == cudaSuccess;
+    if (ok && h->prec == TPFA_MIXED && !h->h_diag)
+        ok = dev_alloc((void**)&h->h_diag, sizeof(double) * (size_t)h->N) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(TPFA_ERR_OOM, "device allocation failed for the host-buffer entry point");
+    }
+    cudaError_t e = cudaMemcpyAsync(h->h_p, p_host, pb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pressure upload");
+    const void* saved = h->p;
+    h->p = h->h_p;
+    rc = launch(h, AsmKernel::YMarch, h->h_R, h->h_vals, h->prec == TPFA_MIXED ? h->h_diag : nullptr, st);
+    h->p = saved;
+    if (rc) return rc;
+    if (R_host) e = cudaMemcpyAsync(R_host, h->h_R, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(vals_host, h->h_vals, vb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && diag64_host && h->prec == TPFA_MIXED)
+        e = cudaMemcpyAsync(diag64_host, h->h_diag, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "result download");
+    return TPFA_OK;
+}
+
+int tpfa_get_pattern(tpfa_handle h, const long long** row_ptr_dev, const int** col_idx_dev, long long* nnz,
+                     void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    DeviceGuard dg(h->device);
+    if (!h->row_ptr) {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        void *rp = nullptr, *ci = nullptr;
+        if (dev_alloc(&rp, sizeof(long long) * (size_t)(h->N + 1)) != cudaSuccess ||
+            dev_alloc(&ci, sizeof(int) * (size_t)h->nnz) != cudaSuccess) {
+            cudaGetLastError();
+            dev_free(rp);
+            dev_free(ci);
+            return fail(TPFA_ERR_OOM, "device allocation failed for the pattern (nnz %lld)", h->nnz);
+        }
+        cudaError_t e = launch_pattern(h->geom, (long long*)rp, (int*)ci, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            dev_free(rp);
+            dev_free(ci);
+            return cuda_fail(e, "pattern build");
+        }
+        h->row_ptr = (long long*)rp;
+        h->col_idx = (int*)ci;
+    }
+    if (row_ptr_dev) *row_ptr_dev = h->row_ptr;
+    if (col_idx_dev) *col_idx_dev = h->col_idx;
+    if (nnz) *nnz = h->nnz;
+    return TPFA_OK;
+}
+
+long long tpfa_nnz(int nx, int ny, int nz, int connectivity) {
+    if (nx < 1 || ny < 1 || nz < 1 || (connectivity != 6 && connectivity != 10))
+        return fail(TPFA_ERR_INVALID_ARG, "bad grid size or connectivity");
+    return total_nnz(GridGeom{nx, ny, nz, connectivity == 10 ? 1 : 0});
+}
+
+int tpfa_copy_pattern(tpfa_handle h, long long* row_ptr_out_dev, int* col_idx_out_dev, void* stream) {
+    int rc = tpfa_get_pattern(h, nullptr, nullptr, nullptr, stream);
+    if (rc) return rc;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (row_ptr_out_dev)
+        e = cudaMemcpyAsync(row_ptr_out_dev, h->row_ptr, sizeof(long long) * (size_t)(h->N + 1),
+                            cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && col_idx_out_dev)
+        e = cudaMemcpyAsync(col_idx_out_dev, h->col_idx, sizeof(int) * (size_t)h->nnz, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pattern copy");
+    return TPFA_OK;
+}
+
+int tpfa_grid_info(tpfa_handle h, int* nx, int* ny, int* nz, int* connectivity, long long* nnz, int* precision) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (nx) *nx = h->nx;
+    if (ny) *ny = h->ny;
+    if (nz) *nz = h->nz;
+    if (connectivity) *connectivity = h->prm.connectivity;
+    if (nnz) *nnz = h->nnz;
+    if (precision) *precision = (int)h->prec;
+    return TPFA_OK;
+}
+
+int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (which < 0 || which > 4 || !out_dev) return fail(TPFA_ERR_INVALID_ARG, "bad transmissibility index or NULL output");
+    if (which >= 3 && !h->geom.diag) return fail(TPFA_ERR_INVALID_ARG, "diagonal links need 10-point connectivity");
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaMemcpyAsync(out_dev, h->T[which], h->real_size * (size_t)h->N, cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "transmissibility copy");
+    return TPFA_OK;
+}
+
+int tpfa_sync_status(tpfa_handle h, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int s = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&s, h->status, sizeof s, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && s) e = cudaMemset(h->status, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (s & STATUS_NONFINITE) return fail(TPFA_ERR_NONFINITE, "a residual or Jacobian value was NaN or Inf");
+    return TPFA_OK;
+}
+
+int tpfa_destroy(tpfa_handle h) {
+    if (!h) return TPFA_OK;
+    {
+        DeviceGuard dg(h->device);
+        cudaDeviceSynchronize();
+        h->release();
+    }
+    delete h;
+    return TPFA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// tpfa_common.cuh -- device-side building blocks shared by the TPFA kernels.
+//
+// Physics (arXiv 2304.11274, Section 3): Eq. density for rho(p), Eq. flux-calc
+// for the two-point flux with single-point upwinding, Eq. vk for the
+// accumulation term.  Every link function here is written with explicit
+// round-to-nearest intrinsics so that the naive, tiled and batched kernels,
+// whichever cell computes a link, produce bit-identical values.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tpfa_grid.h"
+
+namespace tpfa {
+
+// ---------------------------------------------------------------- geometry
+
+// Links of cell index i along an axis of n cells: to i-1 and to i+1.
+__host__ __device__ __forceinline__ int axis_links(int i, int n) { return (i > 0) + (i < n - 1); }
+
+// Links from all cells i' < i along an axis of n cells.
+__host__ __device__ __forceinline__ long long axis_links_before(int i, int n) {
+    return (long long)(i > 1 ? i - 1 : 0) + (i < n - 1 ? i : n - 1);
+}
+
+// CSR offset of the first entry of row (i, j, k).  A row holds the cell
+// itself and adj(K) (Section 5.1), so its length is
+//   1 + ex(i) + ey(j) + ez(k) + diag * ex(i) * ey(j);
+// summing that over all cells before (i, j, k) in x-fastest order gives this
+// closed form, so the kernels never read row_ptr.
+__host__ __device__ __forceinline__ long long row_start(const GridGeom& g, int i, int j, int k) {
+    const long long nx = g.nx, ny = g.ny;
+    const long long Ex = 2 * (nx - 1), Ey = 2 * (ny - 1);
+    const long long D = g.diag;
+    const long long plane = nx * ny + Ex * ny + nx * Ey + D * Ex * Ey;
+    const int ez = axis_links(k, g.nz), ey = axis_links(j, g.ny);
+    long long s = (long long)k * plane + nx * ny * axis_links_before(k, g.nz);
+    s += (long long)j * (nx + Ex + nx * ez) + axis_links_before(j, g.ny) * (nx + D * Ex);
+    s += (long long)i * (1 + ey + ez) + axis_links_before(i, g.nx) * (1 + D * ey);
+    return s;
+}
+
+__host__ __device__ __forceinline__ long long total_nnz(const GridGeom& g) {
+    return row_start(g, 0, 0, g.nz);
+}
+
+__host__ __device__ __forceinline__ int row_length(const GridGeom& g, int i, int j, int k) {
+    const int ex = axis_links(i, g.nx), ey = axis_links(j, g.ny), ez = axis_links(k, g.nz);
+    return 1 + ex + ey + ez + g.diag * ex * ey;
+}
+
+// ---------------------------------------------------------------- FP32 -> FP64
+
+// Exact widening of a float to a double done on the integer pipe.  On GB300
+// the float->double convert instruction issues on the FP64 unit (about two
+// per clock per SM), which the mixed kernels cannot afford per link; this
+// rebuilds the IEEE-754 binary64 bit pattern of normal numbers and zeros
+// (sign kept, exponent rebiased by 1023 - 127 = 896, 23-bit fraction moved up
+// by 29 bits) and leaves subnormals, infinities and NaNs to the hardware.
+__device__ __forceinline__ double widen(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t a = u & 0x7fffffffu;
+    if (a - 0x00800000u < 0x7f000000u) {  // normal: 0x00800000 <= a < 0x7f800000
+        const uint32_t hi = ((a >> 3) + 0x38000000u) | (u & 0x80000000u);
+        return __hiloint2double((int)hi, (int)(u << 29));
+    }
+    if (a == 0u) return __hiloint2double((int)u, 0);  // signed zero
+    return (double)x;
+}
+
+// Narrowing of a finite, normal-range double to a float by truncating the
+// fraction (error below one float ulp), on the integer pipe.  Used only where
+// the value is a small additive term of a compensated FP32 sum.
+__device__ __forceinline__ float narrow_rz(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x);
+    const uint32_t lo = (uint32_t)__double2loint(x);
+    const uint32_t ex = (hi >> 20) & 0x7ffu;
+    if (ex > 896u && ex < 1151u) {
+        const uint32_t f = ((hi & 0x000fffffu) << 3) | (lo >> 29);
+        return __uint_as_float((hi & 0x80000000u) | ((ex - 896u) << 23) | f);
+    }
+    return (float)x;
+}
+
+// ---------------------------------------------------------------- Kahan
+
+struct Kahan32 {
+    float s = 0.f, c = 0.f;  // running sum and compensation; value = s - c
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+};
+
+// ---------------------------------------------------------------- cell state
+
+template <typename T>
+struct CellVal {
+    T p, z, rho, drho;  // pressure, depth, density, d rho / dp
+};
+
+struct PhysF {
+    float rho_ref, p_ref, c_f, inv_mu, g, half_g, V_dt, c_r;
+};
+struct PhysD {
+    double rho_ref, p_ref, c_f, inv_mu, g, half_g, V_dt, c_r;
+};
+
+// Eq. density: rho = rho_ref exp(c_f (p - p_ref)), and its derivative.
+__device__ __forceinline__ CellVal<float> make_cell(const PhysF& q, float p, float z) {
+    CellVal<float> c;
+    c.p = p;
+    c.z = z;
+    c.rho = __fmul_rn(q.rho_ref, expf(__fmul_rn(q.c_f, __fsub_rn(p, q.p_ref))));
+    c.drho = __fmul_rn(q.c_f, c.rho);
+    return c;
+}
+__device__ __forceinline__ CellVal<double> make_cell(const PhysD& q, double p, double z) {
+    CellVal<double> c;
+    c.p = p;
+    c.z = z;
+    c.rho = __dmul_rn(q.rho_ref, exp(__dmul_rn(q.c_f, __dsub_rn(p, q.p_ref))));
+    c.drho = __dmul_rn(q.c_f, c.rho);
+    return c;
+}
+
+// ---------------------------------------------------------------- one link
+
+template <typename T>
+struct LinkOut {
+    T F;   // F_ab: mass outflow from a to b
+    T Da;  // dF_ab / dp_a
+    T Db;  // dF_ab / dp_b
+};
+
+// Two-point flux of Eq. flux-calc seen from row a (z = depth, positive down):
+//   dPhi = (p_a - p_b) - rho_avg g (z_a - z_b)
+//   upstream = a if dPhi > 0 else b,  F = T (rho_up / mu) dPhi
+// and its two pressure derivatives.  Negating every input that changes sign
+// between the two ends of a link negates every output, so F_ba = -F_ab
+// exactly (except the derivatives at an exact tie dPhi == 0, where each end
+// takes the other cell as upstream).
+__device__ __forceinline__ LinkOut<float> link(const PhysF& q, float T, const CellVal<float>& a,
+                                               const CellVal<float>& b) {
+    const float dp = __fsub_rn(a.p, b.p);
+    const float gdz = __fmul_rn(q.g, __fsub_rn(a.z, b.z));
+    const float hgdz = __fmul_rn(q.half_g, __fsub_rn(a.z, b.z));
+    const float rbar = __fmul_rn(0.5f, __fadd_rn(a.rho, b.rho));
+    const float dphi = __fmaf_rn(-rbar, gdz, dp);
+    const bool up_a = dphi > 0.f;
+    const float Tl = __fmul_rn(T, __fmul_rn(up_a ? a.rho : b.rho, q.inv_mu));
+    const float w = __fmul_rn(__fmul_rn(T, q.inv_mu), dphi);
+    LinkOut<float> r;
+    r.F = __fmul_rn(Tl, dphi);
+    const float dda = __fmaf_rn(-a.drho, hgdz, 1.f);
+    const float ddb = __fmaf_rn(-b.drho, hgdz, -1.f);
+    r.Da = __fmaf_rn(Tl, dda, up_a ? __fmul_rn(a.drho, w) : 0.f);
+    r.Db = __fmaf_rn(Tl, ddb, up_a ? 0.f : __fmul_rn(b.drho, w));
+    return r;
+}
+
+__device__ __forceinline__ LinkOut<double> link(const PhysD& q, double T, const CellVal<double>& a,
+                                                const CellVal<double>& b) {
+    const double dp = __dsub_rn(a.p, b.p);
+    const double gdz = __dmul_rn(q.g, __dsub_rn(a.z, b.z));
+    const double hgdz = __dmul_rn(q.half_g, __dsub_rn(a.z, b.z));
+    const double rbar = __dmul_rn(0.5, __dadd_rn(a.rho, b.rho));
+    const double dphi = __fma_rn(-rbar, gdz, dp);
+    const bool up_a = dphi > 0.0;
+    const double Tl = __dmul_rn(T, __dmul_rn(up_a ? a.rho : b.rho, q.inv_mu));
+    const double w = __dmul_rn(__dmul_rn(T, q.inv_mu), dphi);
+    LinkOut<double> r;
+    r.F = __dmul_rn(Tl, dphi);
+    const double dda = __fma_rn(-a.drho, hgdz, 1.0);
+    const double ddb = __fma_rn(-b.drho, hgdz, -1.0);
+    r.Da = __fma_rn(Tl, dda, up_a ? __dmul_rn(a.drho, w) : 0.0);
+    r.Db = __fma_rn(Tl, ddb, up_a ? 0.0 : __dmul_rn(b.drho, w));
+    return r;
+}
+
+// ---------------------------------------------------------------- accumulation
+
+// Accumulation term of Eq. vk, A = (V/dt)(phi(p) rho(p) - phi^n rho^n), and
+// dA/dp.  With mn = (V/dt) phi(p^n) rho(p^n) precomputed in FP64:
+//   phi(p) rho(p) - phi^n rho^n = phi0 c_r (p - p^n) rho(p) + phi^n rho^n expm1(c_f (p - p^n)),
+// which forms the small difference without cancellation.
+struct AccF {
+    double A;  // FP64 accumulation term
+    float dA;  // its pressure derivative (a term of the FP32 diagonal sum)
+};
+
+template <bool CR>
+__device__ __forceinline__ AccF accumulation(const PhysF& q, float p, float pn, double mn, float rho,
+                                             float phi0) {
+    const float dpn = __fsub_rn(p, pn);
+    const float e = expm1f(__fmul_rn(q.c_f, dpn));
+    AccF r;
+    r.A = __dmul_rn(mn, widen(e));
+    if (CR) {
+        // (V/dt) phi0 c_r (p - p^n) rho(p), and dA = (V/dt)(phi0 c_r rho + phi(p) c_f rho)
+        const float vphi = __fmul_rn(q.V_dt, phi0);
+        r.A = __dadd_rn(r.A, widen(__fmul_rn(__fmul_rn(vphi, q.c_r), __fmul_rn(dpn, rho))));
+        const float phi_rel = __fmaf_rn(q.c_r, __fsub_rn(p, q.p_ref), 1.f);
+        r.dA = __fmul_rn(__fmul_rn(vphi, rho), __fmaf_rn(phi_rel, q.c_f, q.c_r));
+    } else {
+        // phi = phi0: (V/dt) phi0 rho(p) = mn exp(c_f (p - p^n))
+        r.dA = __fmul_rn(__fmul_rn(q.c_f, narrow_rz(mn)), __fadd_rn(1.f, e));
+    }
+    return r;
+}
+
+struct AccD {
+    double A, dA;
+};
+
+template <bool CR>
+__device__ __forceinline__ AccD accumulation(const PhysD& q, double p, double pn, double mn, double rho,
+                                             double phi0) {
+    const double dpn = __dsub_rn(p, pn);
+    const double e = expm1(__dmul_rn(q.c_f, dpn));
+    AccD r;
+    r.A = __dmul_rn(mn, e);
+    if (CR) {
+        const double vphi = __dmul_rn(q.V_dt, phi0);
+        r.A = __fma_rn(__dmul_rn(vphi, q.c_r), __dmul_rn(dpn, rho), r.A);
+        const double phi_rel = __fma_rn(q.c_r, __dsub_rn(p, q.p_ref), 1.0);
+        r.dA = __dmul_rn(__dmul_rn(vphi, rho), __fma_rn(phi_rel, q.c_f, q.c_r));
+    } else {
+        r.dA = __dmul_rn(__dmul_rn(q.c_f, mn), __dadd_rn(1.0, e));
+    }
+    return r;
+}
+
+// Non-finite test on the integer pipe (exponent all ones).
+__device__ __forceinline__ bool nonfinite(double x) {
+    return ((uint32_t)__double2hiint(x) & 0x7ff00000u) == 0x7ff00000u;
+}
+
+}  // namespace tpfa

@@ -1,0 +1,46 @@
+// tpfa_impl.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/tpfa.h"
+#include "tpfa_grid.h"
+
+namespace tpfa {
+
+struct PhysF;
+struct PhysD;
+
+enum class AsmKernel { Naive, YMarch };
+
+cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk,
+                                  const AsmFields<float>& f, const AsmOut<float>& o, int JY,
+                                  cudaStream_t st);
+cudaError_t launch_assemble_fp64(AsmKernel kern, const GridGeom& g, const PhysD& q, bool crk,
+                                 const AsmFields<double>& f, const AsmOut<double>& o, int JY,
+                                 cudaStream_t st);
+
+// Setup kernels (tpfa_setup.cu).
+struct SetupPhys {
+    double dx, dy, dz;
+    double rho_ref, p_ref, c_f, c_r, V_dt;
+};
+// Owned transmissibilities from permeability, computed in FP64 and stored as
+// `Real` (float or double).  Tpp/Tmp may be null with 6-point connectivity.
+cudaError_t launch_transmissibility_f32(const GridGeom& g, const SetupPhys& s, const double* perm,
+                                        float* Tx, float* Ty, float* Tz, float* Tpp, float* Tmp,
+                                        cudaStream_t st);
+cudaError_t launch_transmissibility_f64(const GridGeom& g, const SetupPhys& s, const double* perm,
+                                        double* Tx, double* Ty, double* Tz, double* Tpp, double* Tmp,
+                                        cudaStream_t st);
+cudaError_t launch_convert_f32(const double* in, float* out, long long n, cudaStream_t st);
+cudaError_t launch_copy_f64(const double* in, double* out, long long n, cudaStream_t st);
+// m^n = (V/dt) phi(p^n) rho(p^n) in FP64 from p^n of either field type.
+cudaError_t launch_prev_mass_f32(const SetupPhys& s, const float* pn, const double* phi0, double* mn,
+                                 long long n, cudaStream_t st);
+cudaError_t launch_prev_mass_f64(const SetupPhys& s, const double* pn, const double* phi0, double* mn,
+                                 long long n, cudaStream_t st);
+// CSR pattern (row_ptr int64 N+1, col_idx int32 nnz).
+cudaError_t launch_pattern(const GridGeom& g, long long* row_ptr, int* col_idx, cudaStream_t st);
+
+}  // namespace tpfa
