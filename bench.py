@@ -164,7 +164,7 @@ def run_ours(args):
     from paper_2304_11274_gb300.api import Grid
 
     libbuild.build()
-    nx, ny, nz = SHAPE
+    nx, ny, nz = args.shape
     prob = synth.make_problem(nx, ny, nz, synth.BASE_SEED + 1 + 100 * rank, connectivity=CONN)
     pres = [prob.p] + synth.pressure_sequence(prob, 7, seed=synth.BASE_SEED + 11 + 100 * rank)
     g = Grid(nx, ny, nz, prob.phys, "mixed", prob.perm, prob.poro, prob.depth, device=dev)
@@ -223,26 +223,28 @@ def run_ours(args):
     traffic = profiled_traffic(khash)
 
     # end to end: host buffers through the C ABI (H2D of p, D2H of R, values, diag64)
-    import torch as _t
-    ph = [_t.as_tensor(x.astype(np.float32)).pin_memory() for x in pres[:2]]
-    Rh = _t.empty(prob.n, dtype=_t.float64).pin_memory()
-    vh = _t.empty(g.nnz, dtype=_t.float32).pin_memory()
-    dh = _t.empty(prob.n, dtype=_t.float64).pin_memory()
-    g.assemble_jacobian_host(ph[0], Rh, vh, dh)
-    e2e_steps = max(3, min(args.steps, 10))
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    te = time.perf_counter()
-    for s in range(e2e_steps):
-        g.assemble_jacobian_host(ph[s % 2], Rh, vh, dh)
-    e2e_s = time.perf_counter() - te
-    es = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(es, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = cells * e2e_steps / float(es.item())
-    h2d = prob.n * 4
-    d2h = prob.n * 8 + g.nnz * 4 + prob.n * 8
+    e2e = None
+    if not args.no_e2e:
+        ph = [torch.as_tensor(x.astype(np.float32)).pin_memory() for x in pres[:2]]
+        Rh = torch.empty(prob.n, dtype=torch.float64).pin_memory()
+        vh = torch.empty(g.nnz, dtype=torch.float32).pin_memory()
+        dh = torch.empty(prob.n, dtype=torch.float64).pin_memory()
+        g.assemble_jacobian_host(ph[0], Rh, vh, dh)
+        e2e_steps = max(3, min(args.steps, 10))
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter()
+        for s in range(e2e_steps):
+            g.assemble_jacobian_host(ph[s % 2], Rh, vh, dh)
+        e2e_s = time.perf_counter() - te
+        es = torch.tensor([e2e_s], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(es, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": cells * e2e_steps / float(es.item()), "unit": "cells/s",
+               "h2d_bytes_per_step": prob.n * 4, "d2h_bytes_per_step": prob.n * 8 + g.nnz * 4 + prob.n * 8,
+               "steps": e2e_steps, "api": "tpfa_assemble_jacobian_host (pinned host buffers)"}
+        del ph, Rh, vh, dh
 
     # the plain FP64 path on the same grid, for the mixed-vs-FP64 line
     fp64 = None
@@ -286,7 +288,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded; log10 k ~ N(-13, 0.5), phi0 ~ U[0.1, 0.3], hydrostatic + U[-1e5, 1e5] Pa)",
-        "config": {"workload": WORKLOAD, "grid": list(SHAPE), "cells": prob.n, "links_per_cell": CONN,
+        "config": {"workload": WORKLOAD if tuple(args.shape) == SHAPE else
+                   "tpfa_residual_jacobian_%dx%dx%d_10pt_mixed" % tuple(args.shape), "grid": list(args.shape), "cells": prob.n, "links_per_cell": CONN,
                    "nnz": g.nnz, "precision": "mixed: FP32 flux + Kahan residual, FP64 accumulation/diagonal/R",
                    "l2": "inputs+outputs 6.7 GB per step > 129 MB L2; no flush",
                    "pressure_vectors": len(pres), "parallelism": f"replicas x{world}"},
@@ -294,8 +297,7 @@ def run_ours(args):
                      "traffic": traffic, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
                      "kernel": "k_assemble_ymarch<float,DIAG,!CR,JAC>", "kernel_source_sha256_16": khash},
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps, "api": "tpfa_assemble_jacobian_host (pinned host buffers)"},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "fp64": fp64,
     }
@@ -368,6 +370,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
+                    help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
