@@ -186,6 +186,49 @@ int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* str
  */
 int tpfa_sync_status(tpfa_handle h, void* stream);
 
+/* Size of the fixed device workspace of tpfa_assemble_jacobian_static. */
+#define TPFA_STATIC_WORKSPACE_BYTES (64ULL * 1024ULL * 1024ULL)
+
+/*
+ * Residual and Jacobian with NO device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * call cudaMalloc (an application whose own pooled allocator has reserved
+ * the GPU, a process with a hard device-memory budget, code running where
+ * new allocations are not allowed).  It computes exactly what
+ * tpfa_create_grid + tpfa_set_state + tpfa_assemble_jacobian compute, with
+ * the same kernels, but keeps every intermediate array in one fixed
+ * workspace: a file-scope device array of TPFA_STATIC_WORKSPACE_BYTES
+ * (64 MiB) that every GPU which loads the library holds until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   nx, ny, nz, prm, prec, perm_dev, poro_dev, depth_dev : as tpfa_create_grid
+ *   p_dev, p_prev_dev : as tpfa_set_state (field type of `prec`)
+ *   R_dev, vals_dev, diag64_dev : as tpfa_assemble_jacobian (CSR order of the
+ *       pattern; tpfa_nnz gives the length of vals_dev)
+ *   status_dev : optional device word; if non-NULL it is set (asynchronously)
+ *       to 1 when an assembled value is NaN/Inf and to 0 otherwise
+ *   stream     : cudaStream_t as void*; the call is asynchronous on it
+ *
+ * Limits: the workspace holds, per cell, the owned transmissibilities, m^n
+ * (FP64) and on the mixed path the FP32 depth (and FP32 phi0 when c_r != 0):
+ * 32 bytes per cell with 10 links on the mixed path (36 with c_r != 0, so
+ * about 2.09 M and 1.86 M cells) and 48 bytes on the FP64 path (about
+ * 1.39 M cells).  Larger grids return TPFA_ERR_TOO_LARGE, with a message
+ * giving the bytes needed, before any device work; use the handle API for
+ * them.
+ *
+ * The workspace is shared by every call and keeps the last call's contents;
+ * each call overwrites what it reads and clears its error word first.  Calls
+ * whose GPU work overlaps (other streams or host threads without ordering)
+ * race on it.  The first call on each device looks up the workspace's device
+ * address with that device current and caches it; make that first call
+ * before any stream capture.
+ */
+int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_params* prm, tpfa_precision prec,
+                                  const double* perm_dev, const double* poro_dev, const double* depth_dev,
+                                  const void* p_dev, const void* p_prev_dev, double* R_dev, void* vals_dev,
+                                  double* diag64_dev, unsigned int* status_dev, void* stream);
+
 /* Free everything the handle owns; NULL-safe.  Synchronises the device. */
 int tpfa_destroy(tpfa_handle h);
 

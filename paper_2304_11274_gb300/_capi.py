@@ -64,6 +64,7 @@ SIGNATURES = [
     ("tpfa_grid_info", _I, [_VP] + [ctypes.POINTER(_I)] * 4 + [ctypes.POINTER(_LL), ctypes.POINTER(_I)]),
     ("tpfa_get_transmissibility", _I, [_VP, _I, _VP, _VP]),
     ("tpfa_sync_status", _I, [_VP, _VP]),
+    ("tpfa_assemble_jacobian_static", _I, [_I, _I, _I, ctypes.POINTER(TPFAParams), _I] + [_VP] * 10),
     ("tpfa_destroy", _I, [_VP]),
     ("tpfa_last_error_string", ctypes.c_char_p, []),
     ("tpfa_version", _I, []),

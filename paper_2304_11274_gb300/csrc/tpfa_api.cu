@@ -68,6 +68,11 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace tpfa {
+// Error reporting for entry points defined in other translation units.
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace tpfa
+
 struct tpfa_grid {
     int device = 0;
     int nx = 0, ny = 0, nz = 0;

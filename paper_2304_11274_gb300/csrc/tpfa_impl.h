@@ -40,6 +40,9 @@ cudaError_t launch_prev_mass_f32(const SetupPhys& s, const float* pn, const doub
                                  long long n, cudaStream_t st);
 cudaError_t launch_prev_mass_f64(const SetupPhys& s, const double* pn, const double* phi0, double* mn,
                                  long long n, cudaStream_t st);
+// Sets the thread-local message of tpfa_last_error_string and returns code.
+int report_error(int code, const char* msg);
+
 // CSR pattern (row_ptr int64 N+1, col_idx int32 nnz).
 cudaError_t launch_pattern(const GridGeom& g, long long* row_ptr, int* col_idx, cudaStream_t st);
 
