@@ -181,6 +181,54 @@ __device__ __forceinline__ LinkOut<double> link(const PhysD& q, double T, const 
     return r;
 }
 
+// ---------------------------------------------------------------- packed FP32x2
+//
+// Two links evaluated at once with the FP32x2 instructions of sm_100+ (each
+// half rounds exactly like the scalar instruction, so link2() returns, in
+// each half, the bits link() returns for that link).
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+struct Link2 {
+    float2 F, Da, Db;  // .x: first link, .y: second link
+};
+
+__device__ __forceinline__ Link2 link2(const PhysF& q, float2 T, const CellVal<float>& a, const CellVal<float>& b0,
+                                       const CellVal<float>& b1) {
+    const float2 dp = __fadd2_rn(f2(a.p), neg2(f2(b0.p, b1.p)));
+    const float2 dz = __fadd2_rn(f2(a.z), neg2(f2(b0.z, b1.z)));
+    const float2 gdz = __fmul2_rn(f2(q.g), dz);
+    const float2 hgdz = __fmul2_rn(f2(q.half_g), dz);
+    const float2 rbar = __fmul2_rn(f2(0.5f), __fadd2_rn(f2(a.rho), f2(b0.rho, b1.rho)));
+    const float2 dphi = __ffma2_rn(neg2(rbar), gdz, dp);
+    const bool u0 = dphi.x > 0.f, u1 = dphi.y > 0.f;
+    const float2 Tl = __fmul2_rn(T, __fmul2_rn(f2(u0 ? a.rho : b0.rho, u1 ? a.rho : b1.rho), f2(q.inv_mu)));
+    const float2 w = __fmul2_rn(__fmul2_rn(T, f2(q.inv_mu)), dphi);
+    Link2 r;
+    r.F = __fmul2_rn(Tl, dphi);
+    const float2 dda = __ffma2_rn(neg2(f2(a.drho)), hgdz, f2(1.f));
+    const float2 ddb = __ffma2_rn(neg2(f2(b0.drho, b1.drho)), hgdz, f2(-1.f));
+    const float2 ta = __fmul2_rn(f2(a.drho), w);
+    const float2 tb = __fmul2_rn(f2(b0.drho, b1.drho), w);
+    r.Da = __ffma2_rn(Tl, dda, f2(u0 ? ta.x : 0.f, u1 ? ta.y : 0.f));
+    r.Db = __ffma2_rn(Tl, ddb, f2(u0 ? 0.f : tb.x, u1 ? 0.f : tb.y));
+    return r;
+}
+
+// Kahan summation of two independent sums at once (.x and .y), each half
+// identical to Kahan32 on its own.
+struct Kahan2 {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 x) {
+        const float2 y = __fadd2_rn(x, neg2(c));
+        const float2 t = __fadd2_rn(s, y);
+        c = __fadd2_rn(__fadd2_rn(t, neg2(s)), neg2(y));
+        s = t;
+    }
+};
+
 // ---------------------------------------------------------------- accumulation
 
 // Accumulation term of Eq. vk, A = (V/dt)(phi(p) rho(p) - phi^n rho^n), and

@@ -1,0 +1,502 @@
+// tpfa_ymarch.cuh -- the production assembly kernel (sm_103a).
+//
+// A warp owns a 32-cell x-segment (cells i0 .. i0+31) of one z-plane k and
+// marches along y over a run of JY rows; a block stacks W warps on W
+// consecutive planes (their vertical neighbours then hit in L1).  Per row j
+// each lane assembles row (i, j, k) of Algorithm 1 / Eq. vk:
+//
+//   * rows j-1, j, j+1 of (p, z, rho, rho') live in registers ({c, m, p} =
+//     the lane's cell and its x-neighbours, obtained by shuffles; lanes 0 and
+//     31 carry the halo cells i0-1 and i0+32), so each density is evaluated
+//     once per row it enters;
+//   * seven links are evaluated from the lane's own side: -z, -x, +x, the
+//     three links into row j+1 (-x+y, +y, +x+y) and +z;
+//   * the three links into row j-1 are the negations of the previous step's
+//     links into row j (the lane's own +y, the left neighbour's +x+y and the
+//     right neighbour's -x+y, fetched by shuffles): F_LK = -F_KL and the two
+//     derivatives swap and change sign, bit for bit.  Lanes 0 and 31 evaluate
+//     the one such link whose far end lies in the halo.  An exact tie
+//     dPhi == 0 breaks that symmetry (each end takes the other cell as
+//     upstream), so a warp that meets one re-evaluates those links directly;
+//   * rows with all ten neighbours (the interior) take a path with fixed slot
+//     positions; boundary rows use per-slot validity masks;
+//   * the warp's Jacobian rows form one contiguous CSR segment whose offset is
+//     a closed form of (i0, j, k); values are staged in shared memory at their
+//     offsets and written with 16-byte stores;
+//   * every input of row j+2 is requested with cp.async into a per-warp
+//     shared-memory ring at the start of step j, so loads are in flight a
+//     whole step ahead without holding registers.  Registers are capped at
+//     128 for FP32 (16 warps per SM) and 255 for FP64 (whose bound is the
+//     FP64 pipe, not latency).
+//
+// Every value goes through the same link()/accumulation() arithmetic and the
+// same summation order as assemble_row(), so this kernel and the naive one
+// produce identical bits.
+#pragma once
+
+#include <type_traits>
+
+#include "tpfa_row.cuh"
+
+namespace tpfa {
+
+template <typename Real>
+struct YRow {
+    CellVal<Real> c, m, p;  // cells (i, j), (i-1, j), (i+1, j) of this lane
+};
+
+template <typename Real>
+struct YIn {  // inputs of one row other than p and z
+    Real Tx, Ty, Tz, Tpp, Tmp, pn, phi0;
+    double mn;
+    Real p_zm, z_zm, p_zp, z_zp, Tz_m;
+    Real hT1, hT2;  // lane 0: Tx(i0-1, j), Tpp(i0-1, j-1); lane 31: Tmp(i0+32, j-1)
+};
+
+template <typename Real>
+struct YUp {  // a link from row j-1 into row j, seen from row j-1
+    LinkOut<Real> y, xy, mxy;  // to (i, j), (i+1, j), (i-1, j)
+    bool tie;                  // any of the three had dPhi == 0 exactly
+};
+
+template <typename Real>
+__device__ __forceinline__ Real vshfl_up(Real v) {
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <typename Real>
+__device__ __forceinline__ Real vshfl_down(Real v) {
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+__device__ __forceinline__ float drho_of(const PhysF& q, float rho) { return __fmul_rn(q.c_f, rho); }
+__device__ __forceinline__ double drho_of(const PhysD& q, double rho) { return __dmul_rn(q.c_f, rho); }
+
+// A link and whether it may be an exact tie: dPhi == 0 forces F == 0, so
+// F == 0 on a link with T != 0 flags every tie (and, harmlessly, fluxes that
+// underflow to zero).
+template <typename Real, typename Phys>
+__device__ __forceinline__ LinkOut<Real> link_t(const Phys& q, Real T, const CellVal<Real>& a,
+                                                const CellVal<Real>& b, bool& tie) {
+    const LinkOut<Real> r = link(q, T, a, b);
+    tie = (r.F == Real(0)) && (T != Real(0));
+    return r;
+}
+
+template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
+struct YMarch {
+    using Phys = typename PhysOf<Real>::type;
+    static constexpr int VEC = 16 / (int)sizeof(Real);  // elements per 16-byte store
+
+    const GridGeom& g;
+    const Phys& q;
+    const AsmFields<Real>& f;
+    const AsmOut<Real>& o;
+    int lane, i0, i, k, nx, ny, nxy, kb, ih;
+    bool act, hact, zm, zp, xint, v16;
+    long long base_k, rowA, rowB;
+    int Sx0, ez;
+
+    __device__ __forceinline__ YMarch(const GridGeom& g_, const Phys& q_, const AsmFields<Real>& f_,
+                                      const AsmOut<Real>& o_, int lane_, int i0_, int k_)
+        : g(g_), q(q_), f(f_), o(o_), lane(lane_), i0(i0_), i(i0_ + lane_), k(k_) {
+        nx = g.nx;
+        ny = g.ny;
+        nxy = nx * ny;
+        kb = nxy * k;
+        act = i < nx;
+        ih = lane == 0 ? i0 - 1 : (lane == 31 ? i0 + 32 : -1);
+        hact = ih >= 0 && ih < nx;
+        zm = k > 0;
+        zp = k + 1 < g.nz;
+        xint = i0 > 0 && i0 + 32 < nx;
+        v16 = (reinterpret_cast<uintptr_t>(o.vals) & 15u) == 0;
+        const long long Ex = 2LL * (nx - 1), Ey = 2LL * (ny - 1), D = g.diag;
+        const long long plane = (long long)nx * ny + Ex * ny + (long long)nx * Ey + D * Ex * Ey;
+        ez = axis_links(k, g.nz);
+        base_k = (long long)k * plane + (long long)nxy * axis_links_before(k, g.nz);
+        rowA = nx + Ex + (long long)nx * ez;
+        rowB = nx + D * Ex;
+        Sx0 = (int)axis_links_before(i0, nx);
+    }
+
+    // ---- row inputs, prefetched into a per-warp shared-memory ring of RING
+    // rows with cp.async (4- or 8-byte copies by each lane; lanes whose value
+    // does not exist copy nothing and get zeros).  Field f of row r for lane l
+    // lives at ring[slot(r) * NF * 32 + f * 32 + l].
+    static constexpr int RING = 3;
+    enum { F_P, F_Z, F_HP, F_HZ, F_TX, F_TY, F_TZ, F_TPP, F_TMP, F_PN, F_PHI, F_PZM, F_ZZM, F_TZM, F_PZP, F_ZZP,
+           F_HT1, F_HT2, NF };
+    Real* ring;      // RING * NF * 32 values
+    double* ringm;   // RING * 32 values of m^n
+
+    // Ring slot of row r (r >= -1: the march starts one row above its first row).
+    static __device__ __forceinline__ int slot(int r) { return (r + RING) % RING; }
+
+    __device__ __forceinline__ void cp4(Real* dst, const Real* src, bool valid) const {
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+        const int n = valid ? (int)sizeof(Real) : 0;
+        if constexpr (sizeof(Real) == 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    }
+    __device__ __forceinline__ void cp8(double* dst, const double* src, bool valid) const {
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+    }
+    // Request every input of row r (a row outside the grid requests nothing).
+    __device__ __forceinline__ void issue_row(int r) const {
+        Real* R = ring + slot(r) * (NF * 32) + lane;
+        const bool rv = r >= 0 && r < ny;
+        const int c = kb + nx * (rv ? r : 0) + (act ? i : 0);
+        const bool a = rv && act;
+        cp4(R + F_P * 32, f.p + c, a);
+        cp4(R + F_Z * 32, f.z + c, a);
+        const int ch = kb + nx * (rv ? r : 0) + (hact ? ih : 0);
+        cp4(R + F_HP * 32, f.p + ch, rv && hact);
+        cp4(R + F_HZ * 32, f.z + ch, rv && hact);
+        cp4(R + F_TX * 32, f.Tx + c, a);
+        cp4(R + F_TY * 32, f.Ty + c, a);
+        cp4(R + F_TZ * 32, f.Tz + c, a);
+        if (DIAG) {
+            cp4(R + F_TPP * 32, f.Tpp + c, a);
+            cp4(R + F_TMP * 32, f.Tmp + c, a);
+        }
+        cp4(R + F_PN * 32, f.pn + c, a);
+        if (CRK) cp4(R + F_PHI * 32, f.phi0 + c, a);
+        cp4(R + F_PZM * 32, f.p + (zm ? c - nxy : c), a && zm);
+        cp4(R + F_ZZM * 32, f.z + (zm ? c - nxy : c), a && zm);
+        cp4(R + F_TZM * 32, f.Tz + (zm ? c - nxy : c), a && zm);
+        cp4(R + F_PZP * 32, f.p + (zp ? c + nxy : c), a && zp);
+        cp4(R + F_ZZP * 32, f.z + (zp ? c + nxy : c), a && zp);
+        const bool h1 = rv && lane == 0 && i0 > 0;
+        cp4(R + F_HT1 * 32, f.Tx + (h1 ? c - 1 : c), h1);
+        if (DIAG) {
+            const bool h2l = h1 && r > 0, h2r = rv && lane == 31 && hact && r > 0;
+            cp4(R + F_HT2 * 32, h2l ? f.Tpp + (c - nx - 1) : f.Tmp + (h2r ? c - nx + 1 : c), h2l || h2r);
+        }
+        cp8(ringm + slot(r) * 32 + lane, f.mn + c, a);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    // Wait until every requested row but the most recent one has arrived.
+    __device__ __forceinline__ void wait_all_but_newest() const {
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+    }
+    __device__ __forceinline__ YIn<Real> read_in(int r) const {
+        const Real* R = ring + slot(r) * (NF * 32) + lane;
+        YIn<Real> D;
+        D.Tx = R[F_TX * 32];
+        D.Ty = R[F_TY * 32];
+        D.Tz = R[F_TZ * 32];
+        D.Tpp = DIAG ? R[F_TPP * 32] : Real(0);
+        D.Tmp = DIAG ? R[F_TMP * 32] : Real(0);
+        D.pn = R[F_PN * 32];
+        D.phi0 = CRK ? R[F_PHI * 32] : Real(0);
+        D.mn = ringm[slot(r) * 32 + lane];
+        D.p_zm = R[F_PZM * 32];
+        D.z_zm = R[F_ZZM * 32];
+        D.Tz_m = R[F_TZM * 32];
+        D.p_zp = R[F_PZP * 32];
+        D.z_zp = R[F_ZZP * 32];
+        D.hT1 = R[F_HT1 * 32];
+        D.hT2 = DIAG ? R[F_HT2 * 32] : Real(0);
+        return D;
+    }
+    __device__ __forceinline__ YRow<Real> row_cells(int r) const {
+        const Real* R = ring + slot(r) * (NF * 32) + lane;
+        return make_row(R[F_P * 32], R[F_Z * 32], R[F_HP * 32], R[F_HZ * 32]);
+    }
+
+    __device__ __forceinline__ YRow<Real> make_row(Real po, Real zo, Real ph, Real zh) const {
+        YRow<Real> R;
+        R.c = make_cell(q, po, zo);
+        const CellVal<Real> h = make_cell(q, ph, zh);
+        R.m.p = vshfl_up(R.c.p);
+        R.m.z = vshfl_up(R.c.z);
+        R.m.rho = vshfl_up(R.c.rho);
+        R.p.p = vshfl_down(R.c.p);
+        R.p.z = vshfl_down(R.c.z);
+        R.p.rho = vshfl_down(R.c.rho);
+        if (lane == 0) R.m = h;
+        if (lane == 31) R.p = h;
+        R.m.drho = drho_of(q, R.m.rho);
+        R.p.drho = drho_of(q, R.p.rho);
+        return R;
+    }
+    // Links from row r into row r+1, seen from row r (cells of rows r and r+1).
+    __device__ __forceinline__ YUp<Real> up_links(const YRow<Real>& R, const YRow<Real>& Nx, Real Ty, Real Tpp,
+                                                  Real Tmp) const {
+        YUp<Real> U;
+        bool t0, t1 = false, t2 = false;
+        U.y = link_t(q, Ty, R.c, Nx.c, t0);
+        if (DIAG) {
+            U.xy = link_t(q, Tpp, R.c, Nx.p, t1);
+            U.mxy = link_t(q, Tmp, R.c, Nx.m, t2);
+        }
+        U.tie = t0 || t1 || t2;
+        return U;
+    }
+
+    // Assemble row j.  P, C, N: rows j-1, j, j+1.  Uprev: links from row j-1
+    // into row j.  buf: this step's staging buffer.  Returns the links from
+    // row j into row j+1.
+    template <bool FULL>
+    __device__ __forceinline__ YUp<Real> row(int j, const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
+                                             const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev, Real Tpp_prev,
+                                             Real Tmp_prev, Real* buf) const {
+        const int ey = FULL ? 2 : axis_links(j, ny);
+        const unsigned mask = FULL ? (DIAG ? 0x7ffu : 0x575u) : slot_mask(g, i, j, k);
+        Real Tx_m = vshfl_up(D.Tx);
+        if (lane == 0) Tx_m = D.hT1;
+        const CellVal<Real> zmc = make_cell(q, D.p_zm, D.z_zm);
+        const CellVal<Real> zpc = make_cell(q, D.p_zp, D.z_zp);
+
+        // slot order: 0 (0,0,-1) 1 (-1,-1) 2 (0,-1) 3 (+1,-1) 4 (-1,0) 5 self
+        //             6 (+1,0) 7 (-1,+1) 8 (0,+1) 9 (+1,+1) 10 (0,0,+1)
+        LinkOut<Real> S[NSLOT];
+        LinkOut<Real> E;  // lane 0: its (-1,-1) link; lane 31: its (+1,-1) link
+        if constexpr (sizeof(Real) == 4) {
+            // eight links as four FP32x2 pairs
+            const Link2 x = link2(q, f2(Tx_m, D.Tx), C.c, C.m, C.p);
+            const Link2 yz = link2(q, f2(D.Ty, D.Tz), C.c, N.c, zpc);
+            S[4] = LinkOut<float>{x.F.x, x.Da.x, x.Db.x};
+            S[6] = LinkOut<float>{x.F.y, x.Da.y, x.Db.y};
+            S[8] = LinkOut<float>{yz.F.x, yz.Da.x, yz.Db.x};
+            S[10] = LinkOut<float>{yz.F.y, yz.Da.y, yz.Db.y};
+            if (DIAG) {
+                const Link2 d = link2(q, f2(D.Tmp, D.Tpp), C.c, N.m, N.p);
+                const Link2 ze = link2(q, f2(D.Tz_m, D.hT2), C.c, zmc, lane == 0 ? P.m : P.p);
+                S[7] = LinkOut<float>{d.F.x, d.Da.x, d.Db.x};
+                S[9] = LinkOut<float>{d.F.y, d.Da.y, d.Db.y};
+                S[0] = LinkOut<float>{ze.F.x, ze.Da.x, ze.Db.x};
+                E = LinkOut<float>{ze.F.y, ze.Da.y, ze.Db.y};
+            } else {
+                S[0] = link(q, D.Tz_m, C.c, zmc);
+            }
+        } else {
+            S[0] = link(q, D.Tz_m, C.c, zmc);
+            S[4] = link(q, Tx_m, C.c, C.m);
+            S[6] = link(q, D.Tx, C.c, C.p);
+            S[8] = link(q, D.Ty, C.c, N.c);
+            S[10] = link(q, D.Tz, C.c, zpc);
+            if (DIAG) {
+                S[7] = link(q, D.Tmp, C.c, N.m);
+                S[9] = link(q, D.Tpp, C.c, N.p);
+                E = link(q, D.hT2, C.c, lane == 0 ? P.m : P.p);
+            }
+        }
+        YUp<Real> U;
+        U.y = S[8];
+        U.xy = S[9];
+        U.mxy = S[7];
+        U.tie = (S[8].F == Real(0) && D.Ty != Real(0)) ||
+                (DIAG && ((S[9].F == Real(0) && D.Tpp != Real(0)) || (S[7].F == Real(0) && D.Tmp != Real(0))));
+
+        // links into row j-1: negations of Uprev (own +y, left's +x+y, right's -x+y)
+        S[2] = LinkOut<Real>{-Uprev.y.F, -Uprev.y.Db, -Uprev.y.Da};
+        if (DIAG) {
+            const Real f1 = vshfl_up(Uprev.xy.F), a1 = vshfl_up(Uprev.xy.Da), b1 = vshfl_up(Uprev.xy.Db);
+            const Real f3 = vshfl_down(Uprev.mxy.F), a3 = vshfl_down(Uprev.mxy.Da), b3 = vshfl_down(Uprev.mxy.Db);
+            S[1] = LinkOut<Real>{-f1, -b1, -a1};
+            S[3] = LinkOut<Real>{-f3, -b3, -a3};
+            if (lane == 0) S[1] = E;
+            if (lane == 31) S[3] = E;
+        }
+        if (__any_sync(0xffffffffu, Uprev.tie)) {
+            // an exact tie among row j-1's links: evaluate those links directly
+            S[2] = link(q, Ty_prev, C.c, P.c);
+            if (DIAG) {
+                Real Tl = vshfl_up(Tpp_prev), Tr = vshfl_down(Tmp_prev);
+                if (lane == 0) Tl = D.hT2;
+                if (lane == 31) Tr = D.hT2;
+                S[1] = link(q, Tl, C.c, P.m);
+                S[3] = link(q, Tr, C.c, P.p);
+            }
+        }
+
+        // offsets of this row's CSR segment and of this lane's row in it
+        const int per = 1 + ey + ez, perx = 1 + g.diag * ey;
+        const int lane_off = FULL ? lane * (DIAG ? 11 : 7)
+                                  : (i - i0) * per + (int)(axis_links_before(i, nx) - Sx0) * perx;
+        const long long seg = base_k + (long long)j * rowA + axis_links_before(j, ny) * rowB +
+                              (long long)i0 * per + (long long)Sx0 * perx;
+        const int aoff = JAC ? (int)(seg & (VEC - 1)) : 0;
+
+        const RowSums out = sum_row(S, mask, C.c, D, buf + aoff + lane_off);
+        const int c = kb + nx * j + i;
+        if (act) {
+            if (o.R) o.R[c] = out.R;
+            if (JAC && o.diag64) o.diag64[c] = out.diag64;
+            if (out.bad) atomicOr(o.status, STATUS_NONFINITE);
+        }
+        if (JAC) {
+            const int iend = min(i0 + 32, nx);
+            const int seg_len = (iend - i0) * per + (int)(axis_links_before(iend, nx) - Sx0) * perx;
+            write_segment(buf, seg, aoff, seg_len);
+        }
+        return U;
+    }
+
+    // Slot values go to rowbuf; residual and diagonal sums in slot order.
+    // FP32: one FP32x2 Kahan sum carries (residual, diagonal); FP64: plain sums.
+    __device__ __forceinline__ RowSums sum_row(const LinkOut<Real> (&S)[NSLOT], unsigned mask, const CellVal<Real>& me,
+                                               const YIn<Real>& D, Real* rowbuf) const {
+        if constexpr (sizeof(Real) == 4) {
+            Kahan2 ks;
+#pragma unroll
+            for (int s = 0; s < NSLOT; ++s) {
+                if (s == SLOT_SELF) continue;
+                if (mask & (1u << s)) {
+                    ks.add(f2(S[s].F, JAC ? S[s].Da : 0.f));
+                    if (JAC && act) rowbuf[slot_pos(mask, s)] = S[s].Db;
+                }
+            }
+            const AccF acc = accumulation<CRK>(q, me.p, D.pn, D.mn, me.rho, D.phi0);
+            RowSums out;
+            out.R = __dadd_rn(__dadd_rn(acc.A, widen(ks.s.x)), -widen(ks.c.x));
+            out.diag64 = 0.0;
+            if (JAC) {
+                Kahan32 ds{ks.s.y, ks.c.y};
+                ds.add(acc.dA);
+                out.diag64 = __dadd_rn(widen(ds.s), -widen(ds.c));
+                if (act) rowbuf[slot_pos(mask, SLOT_SELF)] = __fsub_rn(ds.s, ds.c);
+            }
+            out.bad = nonfinite(out.R) || (JAC && nonfinite(out.diag64));
+            return out;
+        } else {
+            double rs = 0.0, ds = 0.0;
+#pragma unroll
+            for (int s = 0; s < NSLOT; ++s) {
+                if (s == SLOT_SELF) continue;
+                if (mask & (1u << s)) {
+                    rs = __dadd_rn(rs, S[s].F);
+                    if (JAC) {
+                        ds = __dadd_rn(ds, S[s].Da);
+                        if (act) rowbuf[slot_pos(mask, s)] = S[s].Db;
+                    }
+                }
+            }
+            const AccD acc = accumulation<CRK>(q, me.p, D.pn, D.mn, me.rho, D.phi0);
+            RowSums out;
+            out.R = __dadd_rn(rs, acc.A);
+            out.diag64 = 0.0;
+            if (JAC) {
+                ds = __dadd_rn(ds, acc.dA);
+                out.diag64 = ds;
+                if (act) rowbuf[slot_pos(mask, SLOT_SELF)] = ds;
+            }
+            out.bad = nonfinite(out.R) || (JAC && nonfinite(out.diag64));
+            return out;
+        }
+    }
+
+    // Wait until the bulk store issued from this buffer two steps ago has
+    // read it (lane 0 issued it), so the buffer can be refilled.
+    __device__ __forceinline__ void buffer_ready() const {
+        if (JAC && v16 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+    }
+
+    // Copy buf[aoff .. aoff+len) to vals[seg .. seg+len).  The 16-byte-aligned
+    // middle goes out as one bulk shared->global copy (issued by lane 0,
+    // tracked as a bulk async-group); the at most 2 (VEC - 1) elements at the
+    // ends are stored by single lanes.
+    __device__ __forceinline__ void write_segment(Real* buf, long long seg, int aoff, int len) const {
+        Real* dst = o.vals + (seg - aoff);  // 16-byte aligned when v16
+        const int span = aoff + len;
+        if (v16) {
+            const int qlo = (aoff + VEC - 1) / VEC, qhi = span / VEC;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (qhi > qlo) {
+                if (lane == 0) {
+                    const uint32_t src = (uint32_t)__cvta_generic_to_shared(buf + qlo * VEC);
+                    const uint32_t bytes = (uint32_t)(qhi - qlo) * 16u;
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+                                 "cp.async.bulk.commit_group;" ::"l"(dst + qlo * VEC), "r"(src), "r"(bytes)
+                                 : "memory");
+                }
+                const int nh = qlo * VEC - aoff, nt = span - qhi * VEC;  // each < VEC
+                if (lane >= 1 && lane <= nh) dst[aoff + lane - 1] = buf[aoff + lane - 1];
+                if (lane >= 8 && lane < 8 + nt) dst[qhi * VEC + lane - 8] = buf[qhi * VEC + lane - 8];
+            } else {
+                if (lane < len) dst[aoff + lane] = buf[aoff + lane];
+            }
+        } else {
+            __syncwarp();
+            for (int e = aoff + lane; e < span; e += 32) dst[e] = buf[e];
+            __syncwarp();
+        }
+    }
+
+    // All bulk stores complete before the block exits.
+    __device__ __forceinline__ void drain() const {
+        if (JAC && v16 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+};
+
+template <typename Real, int W>
+constexpr int ymarch_smem_bytes() {
+    return W * (2 * (32 * NSLOT + 16 / (int)sizeof(Real)) * (int)sizeof(Real) +
+                3 * 18 * 32 * (int)sizeof(Real) + 3 * 32 * (int)sizeof(double));
+}
+
+template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
+__global__ void __launch_bounds__(32 * W, (sizeof(Real) == 4 ? 16 : 8) / W)
+    k_assemble_ymarch(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f, AsmOut<Real> o, int JY) {
+    using M_t = YMarch<Real, DIAG, CRK, JAC, W>;
+    constexpr int BUF = 32 * NSLOT + 16 / (int)sizeof(Real);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int k = blockIdx.z * W + w;
+    if (k >= g.nz) return;  // warp-uniform
+    // per warp: two staging buffers, then the input ring, then the m^n ring
+    Real* stage = reinterpret_cast<Real*>(smem) + w * 2 * BUF;
+    Real* ring = reinterpret_cast<Real*>(smem) + W * 2 * BUF + w * M_t::RING * M_t::NF * 32;
+    double* ringm = reinterpret_cast<double*>(reinterpret_cast<Real*>(smem) + W * 2 * BUF +
+                                              W * M_t::RING * M_t::NF * 32) + w * M_t::RING * 32;
+    M_t M(g, q, f, o, lane, blockIdx.x * 32, k);
+    M.ring = ring;
+    M.ringm = ringm;
+    const int j0 = blockIdx.y * JY;
+    const int j1 = min(j0 + JY, g.ny);
+    const bool zint = M.zm && M.zp;
+
+    // prologue: rows j0-1 and j0 (cells, and the links of row j0-1 into row j0)
+    M.issue_row(j0 - 1);
+    M.issue_row(j0);
+    M.issue_row(j0 + 1);
+    M.wait_all_but_newest();
+    YRow<Real> P = M.row_cells(j0 - 1);
+    YRow<Real> C = M.row_cells(j0);
+    Real Ty_prev, Tpp_prev, Tmp_prev;
+    {
+        const YIn<Real> Dp = M.read_in(j0 - 1);  // zeros when j0 == 0
+        Ty_prev = Dp.Ty;
+        Tpp_prev = Dp.Tpp;
+        Tmp_prev = Dp.Tmp;
+    }
+    YUp<Real> U = M.up_links(P, C, Ty_prev, Tpp_prev, Tmp_prev);
+
+    for (int j = j0; j < j1; ++j) {
+        // row j+2 is requested now and used two steps later; row j+1 arrived
+        M.issue_row(j + 2);
+        M.wait_all_but_newest();
+        const YRow<Real> N = M.row_cells(j + 1);
+        const YIn<Real> D = M.read_in(j);
+        Real* buf = stage + ((j - j0) & 1) * BUF;
+        M.buffer_ready();
+        const bool full = M.xint && zint && j > 0 && j + 1 < M.ny;
+        U = full ? M.template row<true>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf)
+                 : M.template row<false>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf);
+        Ty_prev = D.Ty;
+        Tpp_prev = D.Tpp;
+        Tmp_prev = D.Tmp;
+        P = C;
+        C = N;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    M.drain();
+}
+
+}  // namespace tpfa
