@@ -53,6 +53,7 @@ extern "C" {
 #define TPFA_ERR_NONFINITE (-5)   /* a residual or Jacobian value came out NaN/Inf */
 #define TPFA_ERR_NO_STATE (-6)    /* assemble called before tpfa_set_state */
 #define TPFA_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out */
+#define TPFA_ERR_DEVICE_CHECK (-8) /* a device-side bounds check failed (nothing was accessed) */
 
 typedef struct tpfa_grid* tpfa_handle; /* opaque, library-owned */
 
@@ -151,6 +152,25 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
                                 void* vals_host, double* diag64_host, void* stream);
 
 /*
+ * Replace the permeability (for example while optimising log-permeability):
+ * recomputes the owned transmissibilities and the stored k of the adjoint.
+ * perm_dev: N doubles (m^2, >= 0), read asynchronously on `stream`.
+ */
+int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream);
+
+/*
+ * Adjoint of the residual (vector-Jacobian products) at the bound state:
+ *   g_p[i]   = sum_K v_K dR_K/dp_i              (= J^T v)
+ *   g_lnk[i] = sum_K v_K dR_K/d(ln k_i)         (natural log)
+ * R as in Eq. vk with the flux of Eq. flux-calc; k enters only through the
+ * harmonic transmissibilities, d Upsilon_KL/d ln k_K = Upsilon_KL k_L/(k_K + k_L).
+ * Densities, upwind choices and mobilities are recomputed, nothing is stored
+ * by the forward pass.  v_dev, g_p_dev: N doubles; g_lnk_dev: N doubles or
+ * NULL.  Links in the path's precision, sums and outputs in FP64.
+ */
+int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_dev, void* stream);
+
+/*
  * The static Jacobian pattern: row_ptr (N+1 int64) and col_idx (nnz int32),
  * columns ascending in each row.  Built on the first call (library-owned,
  * read-only, freed by destroy); synchronises `stream` on that first call.
@@ -182,7 +202,9 @@ int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* str
 
 /*
  * Wait for `stream`, then report and clear device-side errors latched since
- * the last call: TPFA_ERR_NONFINITE if any assembled value was NaN/Inf.
+ * the last call: TPFA_ERR_DEVICE_CHECK if a checked device access was out of
+ * range (and skipped), else TPFA_ERR_NONFINITE if any assembled value was
+ * NaN/Inf.
  */
 int tpfa_sync_status(tpfa_handle h, void* stream);
 

@@ -20,6 +20,7 @@ ERRORS = {
     -5: "TPFA_ERR_NONFINITE",
     -6: "TPFA_ERR_NO_STATE",
     -7: "TPFA_ERR_TIMEOUT",
+    -8: "TPFA_ERR_DEVICE_CHECK",
 }
 TPFA_FP64, TPFA_MIXED = 0, 1
 KERNELS = {"auto": 0, "naive": 1, "tiled": 2}
@@ -58,6 +59,8 @@ SIGNATURES = [
     ("tpfa_assemble_jacobian", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_assemble_jacobian_kernel", _I, [_VP, _I, _VP, _VP, _VP, _VP]),
     ("tpfa_assemble_jacobian_host", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    ("tpfa_set_permeability", _I, [_VP, _VP, _VP]),
+    ("tpfa_vjp", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_get_pattern", _I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_LL), _VP]),
     ("tpfa_copy_pattern", _I, [_VP, _VP, _VP, _VP]),
     ("tpfa_nnz", _LL, [_I, _I, _I, _I]),

@@ -143,6 +143,23 @@ class Grid:
                                                    _ptr(diag_host), _stream(stream)))
         return R_host, vals_host, diag_host
 
+    def set_permeability(self, perm, stream=None):
+        """Replace k (m^2); recomputes the transmissibilities on the device."""
+        k = _dev_f64(perm, self.device)
+        if k.numel() != self.n:
+            raise ValueError(f"expected {self.n} values, got {k.numel()}")
+        check(self.lib.tpfa_set_permeability(self.handle, _ptr(k), _stream(stream)))
+        self._perm = k  # read asynchronously: keep it alive
+
+    def vjp(self, v, want_lnk=True, stream=None):
+        """(g_p, g_lnk) = (v^T dR/dp, v^T dR/d ln k) at the bound state, FP64."""
+        v = _dev_f64(v, self.device)
+        g_p = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        g_lnk = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_lnk else None
+        check(self.lib.tpfa_vjp(self.handle, _ptr(v), _ptr(g_p), _ptr(g_lnk), _stream(stream)))
+        self._v = v
+        return g_p, g_lnk
+
     def pattern(self, stream=None):
         """(row_ptr int64[N+1], col_idx int32[nnz]) as device tensors."""
         rp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
@@ -159,4 +176,44 @@ class Grid:
         check(self.lib.tpfa_sync_status(self.handle, _stream(stream)))
 
 
-__all__ = ["Grid", "TPFAError", "PRECISIONS"]
+class TPFAResidual(torch.autograd.Function):
+    """R(p, ln k) of Eq. vk on a Grid whose previous-step state is bound.
+
+    forward(grid, p, log_k) -> R (FP64, N).  log_k is the natural log of the
+    permeability; the grid's transmissibilities are recomputed when it
+    changes.  backward runs the library's adjoint kernel (checkpoint-free:
+    nothing is saved but p and log_k)."""
+
+    @staticmethod
+    def forward(ctx, grid, p, log_k):
+        _apply_log_k(grid, log_k)
+        grid.set_pressure(p.detach())
+        R = grid.assemble_residual()
+        ctx.grid = grid
+        ctx.save_for_backward(p, log_k)
+        return R
+
+    @staticmethod
+    def backward(ctx, gR):
+        p, log_k = ctx.saved_tensors
+        grid = ctx.grid
+        _apply_log_k(grid, log_k)
+        grid.set_pressure(p.detach())
+        g_p, g_lnk = grid.vjp(gR.detach().to(torch.float64).contiguous(), want_lnk=ctx.needs_input_grad[2])
+        gp = g_p.to(p.dtype) if ctx.needs_input_grad[1] else None
+        gk = g_lnk.to(log_k.dtype) if ctx.needs_input_grad[2] else None
+        return None, gp, gk
+
+
+def _apply_log_k(grid, log_k):
+    # Always re-applied: a tensor's address and version do not identify its
+    # contents (the caching allocator reuses addresses).
+    grid.set_permeability(torch.exp(log_k.detach().to(torch.float64)))
+
+
+def residual(grid, p, log_k):
+    """Differentiable residual: TPFAResidual.apply(grid, p, log_k)."""
+    return TPFAResidual.apply(grid, p, log_k)
+
+
+__all__ = ["Grid", "TPFAError", "PRECISIONS", "TPFAResidual", "residual"]

@@ -87,6 +87,7 @@ struct tpfa_grid {
     size_t real_size = 8;
     void* T[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // Tx, Ty, Tz, Tpp, Tmp
     void* z = nullptr;
+    void* kperm = nullptr;  // permeability in the field type (adjoint)
     double* phi0_d = nullptr;
     void* phi0_r = nullptr;  // phi0 in the field type (mixed path with c_r != 0)
     double* mn = nullptr;
@@ -107,6 +108,7 @@ struct tpfa_grid {
     void release() {
         for (auto& t : T) dev_free(t), t = nullptr;
         dev_free(z);
+        dev_free(kperm);
         dev_free(phi0_d);
         dev_free(phi0_r);
         dev_free(mn);
@@ -117,7 +119,7 @@ struct tpfa_grid {
         dev_free(h_R);
         dev_free(h_vals);
         dev_free(h_diag);
-        z = nullptr, phi0_d = nullptr, phi0_r = nullptr, mn = nullptr, status = nullptr;
+        z = nullptr, kperm = nullptr, phi0_d = nullptr, phi0_r = nullptr, mn = nullptr, status = nullptr;
         row_ptr = nullptr, col_idx = nullptr, h_p = nullptr, h_R = nullptr, h_vals = nullptr, h_diag = nullptr;
     }
 };
@@ -149,8 +151,11 @@ AsmFields<Real> fields_of(const tpfa_grid* h) {
     f.Tx = static_cast<const Real*>(h->T[0]);
     f.Ty = static_cast<const Real*>(h->T[1]);
     f.Tz = static_cast<const Real*>(h->T[2]);
-    f.Tpp = static_cast<const Real*>(h->T[3]);
-    f.Tmp = static_cast<const Real*>(h->T[4]);
+    // 6-point grids have no diagonal links; their pointers still name a valid
+    // array so that no load, even one a compiler hoists out of its guard, can
+    // dereference NULL.
+    f.Tpp = static_cast<const Real*>(h->T[3] ? h->T[3] : h->T[0]);
+    f.Tmp = static_cast<const Real*>(h->T[4] ? h->T[4] : h->T[0]);
     return f;
 }
 
@@ -217,6 +222,7 @@ int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params
     bool ok = true;
     for (int t = 0; t < nT && ok; ++t) ok = dev_alloc(&h->T[t], rb) == cudaSuccess;
     ok = ok && dev_alloc(&h->z, rb) == cudaSuccess;
+    ok = ok && dev_alloc(&h->kperm, rb) == cudaSuccess;
     ok = ok && dev_alloc((void**)&h->phi0_d, sizeof(double) * (size_t)N) == cudaSuccess;
     if (ok && h->crk) ok = dev_alloc(&h->phi0_r, rb) == cudaSuccess;
     ok = ok && dev_alloc((void**)&h->mn, sizeof(double) * (size_t)N) == cudaSuccess;
@@ -239,6 +245,9 @@ int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params
     if (e == cudaSuccess)
         e = prec == TPFA_MIXED ? launch_convert_f32(depth_dev, (float*)h->z, N, st)
                                : launch_copy_f64(depth_dev, (double*)h->z, N, st);
+    if (e == cudaSuccess)
+        e = prec == TPFA_MIXED ? launch_store_perm_f32(perm_dev, (float*)h->kperm, N, st)
+                               : launch_store_perm_f64(perm_dev, (double*)h->kperm, N, st);
     if (e == cudaSuccess) e = launch_copy_f64(poro_dev, h->phi0_d, N, st);
     if (e == cudaSuccess && h->crk)
         e = prec == TPFA_MIXED ? launch_convert_f32(poro_dev, (float*)h->phi0_r, N, st)
@@ -345,6 +354,44 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
     return TPFA_OK;
 }
 
+int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!perm_dev) return fail(TPFA_ERR_INVALID_ARG, "perm must be non-NULL");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (h->prec == TPFA_MIXED) {
+        e = launch_transmissibility_f32(h->geom, h->sp, perm_dev, (float*)h->T[0], (float*)h->T[1], (float*)h->T[2],
+                                        (float*)h->T[3], (float*)h->T[4], st);
+        if (e == cudaSuccess) e = launch_store_perm_f32(perm_dev, (float*)h->kperm, h->N, st);
+    } else {
+        e = launch_transmissibility_f64(h->geom, h->sp, perm_dev, (double*)h->T[0], (double*)h->T[1],
+                                        (double*)h->T[2], (double*)h->T[3], (double*)h->T[4], st);
+        if (e == cudaSuccess) e = launch_store_perm_f64(perm_dev, (double*)h->kperm, h->N, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "set_permeability launch");
+    return TPFA_OK;
+}
+
+int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_dev, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!v_dev || !g_p_dev) return fail(TPFA_ERR_INVALID_ARG, "v and g_p must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (h->prec == TPFA_MIXED)
+        e = launch_vjp_mixed(h->geom, h->qf, h->crk, fields_of<float>(h), (const float*)h->kperm, v_dev, g_p_dev,
+                             g_lnk_dev, h->status, st);
+    else
+        e = launch_vjp_fp64(h->geom, h->qd, h->crk, fields_of<double>(h), (const double*)h->kperm, v_dev, g_p_dev,
+                            g_lnk_dev, h->status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
+    return TPFA_OK;
+}
+
 int tpfa_get_pattern(tpfa_handle h, const long long** row_ptr_dev, const int** col_idx_dev, long long* nnz,
                      void* stream) {
     int rc = check_handle(h);
@@ -431,6 +478,7 @@ int tpfa_sync_status(tpfa_handle h, void* stream) {
     if (e == cudaSuccess) e = cudaMemcpy(&s, h->status, sizeof s, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && s) e = cudaMemset(h->status, 0, sizeof(unsigned int));
     if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (s & STATUS_DEVICE_CHECK) return fail(TPFA_ERR_DEVICE_CHECK, "a device-side bounds check failed");
     if (s & STATUS_NONFINITE) return fail(TPFA_ERR_NONFINITE, "a residual or Jacobian value was NaN or Inf");
     return TPFA_OK;
 }

@@ -40,5 +40,6 @@ struct AsmOut {
 };
 
 constexpr unsigned int STATUS_NONFINITE = 1u;
+constexpr unsigned int STATUS_DEVICE_CHECK = 2u;  // a checked device access was out of range
 
 }  // namespace tpfa

@@ -40,6 +40,16 @@ cudaError_t launch_prev_mass_f32(const SetupPhys& s, const float* pn, const doub
                                  long long n, cudaStream_t st);
 cudaError_t launch_prev_mass_f64(const SetupPhys& s, const double* pn, const double* phi0, double* mn,
                                  long long n, cudaStream_t st);
+// Adjoint (tpfa_vjp.cu).
+cudaError_t launch_vjp_mixed(const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
+                             const float* kperm, const double* v, double* g_p, double* g_lnk,
+                             unsigned int* status, cudaStream_t st);
+cudaError_t launch_vjp_fp64(const GridGeom& g, const PhysD& q, bool crk, const AsmFields<double>& f,
+                            const double* kperm, const double* v, double* g_p, double* g_lnk,
+                            unsigned int* status, cudaStream_t st);
+cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st);
+cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st);
+
 // Sets the thread-local message of tpfa_last_error_string and returns code.
 int report_error(int code, const char* msg);
 

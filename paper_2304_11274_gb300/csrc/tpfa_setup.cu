@@ -39,14 +39,17 @@ __global__ void k_trans(GridGeom g, Geo geo, const double* __restrict__ perm, Re
         const int k = (int)(c / nxy);
         const int j = (int)((c - k * nxy) / nx);
         const int i = (int)(c - k * nxy - j * nx);
+        // neighbour indices fall back to c itself where the link does not
+        // exist, so every address formed is inside perm
         const double kc = perm[c];
-        Tx[c] = (Real)(i + 1 < g.nx ? two_point(kc, perm[c + 1], geo.ax) : 0.0);
-        Ty[c] = (Real)(j + 1 < g.ny ? two_point(kc, perm[c + nx], geo.ay) : 0.0);
-        Tz[c] = (Real)(k + 1 < g.nz ? two_point(kc, perm[c + nxy], geo.az) : 0.0);
+        const bool xp = i + 1 < g.nx, yp = j + 1 < g.ny, zp = k + 1 < g.nz;
+        Tx[c] = (Real)(xp ? two_point(kc, perm[xp ? c + 1 : c], geo.ax) : 0.0);
+        Ty[c] = (Real)(yp ? two_point(kc, perm[yp ? c + nx : c], geo.ay) : 0.0);
+        Tz[c] = (Real)(zp ? two_point(kc, perm[zp ? c + nxy : c], geo.az) : 0.0);
         if (g.diag) {
-            const bool yp = j + 1 < g.ny;
-            Tpp[c] = (Real)(yp && i + 1 < g.nx ? two_point(kc, perm[c + nx + 1], geo.ad) : 0.0);
-            Tmp[c] = (Real)(yp && i > 0 ? two_point(kc, perm[c + nx - 1], geo.ad) : 0.0);
+            const bool pp = yp && xp, mp = yp && i > 0;
+            Tpp[c] = (Real)(pp ? two_point(kc, perm[pp ? c + nx + 1 : c], geo.ad) : 0.0);
+            Tmp[c] = (Real)(mp ? two_point(kc, perm[mp ? c + nx - 1 : c], geo.ad) : 0.0);
         }
     }
 }

@@ -134,7 +134,7 @@ extern "C" int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_
                           (float)prm->g, (float)(0.5 * prm->g), (float)V_dt, (float)prm->c_r};
             AsmFields<float> f{(const float*)p_dev, (const float*)p_prev_dev, mn, z, phi,
                                (const float*)T[0], (const float*)T[1], (const float*)T[2],
-                               (const float*)T[3], (const float*)T[4]};
+                               (const float*)(T[3] ? T[3] : T[0]), (const float*)(T[4] ? T[4] : T[0])};
             AsmOut<float> o{R_dev, (float*)vals_dev, diag64_dev, status};
             e = launch_assemble_mixed(AsmKernel::YMarch, g, q, crk, f, o, 32, st);
         }
@@ -147,7 +147,7 @@ extern "C" int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_
             const PhysD q{prm->rho_ref, prm->p_ref, prm->c_f, 1.0 / prm->mu, prm->g, 0.5 * prm->g, V_dt, prm->c_r};
             AsmFields<double> f{(const double*)p_dev, (const double*)p_prev_dev, mn, depth_dev, poro_dev,
                                 (const double*)T[0], (const double*)T[1], (const double*)T[2],
-                                (const double*)T[3], (const double*)T[4]};
+                                (const double*)(T[3] ? T[3] : T[0]), (const double*)(T[4] ? T[4] : T[0])};
             AsmOut<double> o{R_dev, (double*)vals_dev, nullptr, status};
             e = launch_assemble_fp64(AsmKernel::YMarch, g, q, crk, f, o, 32, st);
         }

@@ -1,0 +1,126 @@
+"""Adjoint (VJP) kernel against the oracle's gradient and finite differences."""
+import numpy as np
+import pytest
+import torch
+
+import _compare as C
+import oracle
+from paper_2304_11274_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-6}
+
+
+def _grid(prob, precision):
+    from paper_2304_11274_gb300.api import Grid
+    return Grid(prob.nx, prob.ny, prob.nz, prob.phys, precision, prob.perm, prob.poro, prob.depth)
+
+
+def _normwise(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _gp_reference(prob, v, eps):
+    """J^T v from the oracle's Jacobian, and from its alternative evaluation
+    where upwind choices are ambiguous (either is admissible)."""
+    ref = C.reference(prob, eps)
+    rp, ci = ref["row_ptr"], ref["col_idx"]
+    rows = np.repeat(np.arange(prob.n), np.diff(rp))
+    out = [np.bincount(ci, weights=ref["J"] * v[rows], minlength=prob.n)]
+    if ref["J_alt"] is not None:
+        out.append(np.bincount(ci, weights=ref["J_alt"] * v[rows], minlength=prob.n))
+    return out
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 4), (7, 5, 3), (33, 17, 9), (40, 37, 6)])
+@pytest.mark.parametrize("conn", [6, 10])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("c_r", [0.0, 1e-9])
+def test_vjp_matches_oracle(shape, conn, precision, c_r):
+    prob = synth.make_problem(*shape, seed=17, connectivity=conn, c_r=c_r)
+    if precision == "mixed":
+        prob = synth.round_to_f32(prob)
+        prob.perm = prob.perm.astype(np.float32).astype(np.float64)  # the adjoint's k is stored in FP32
+    v = synth.cotangent(prob.n, seed=3)
+    g_p_ref, g_lnk_ref = oracle.vjp(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                    prob.p, prob.pn, v)
+    with _grid(prob, precision) as g:
+        g.set_state(prob.p, prob.pn)
+        g_p, g_lnk = g.vjp(v)
+        g.sync_status()
+        g_p, g_lnk = g_p.cpu().numpy(), g_lnk.cpu().numpy()
+    eps = C.EPS32 if precision == "mixed" else C.EPS64
+    cands = _gp_reference(prob, v, eps)
+    assert np.allclose(cands[0], g_p_ref, rtol=1e-12, atol=1e-12 * np.abs(g_p_ref).max())
+    e_p = min(_normwise(g_p, c) for c in cands)
+    assert e_p <= TOL[precision], e_p
+    if prob.n > 1:
+        assert _normwise(g_lnk, g_lnk_ref) <= TOL[precision]
+
+
+def test_vjp_adjoint_size_against_oracle():
+    """128^3 with 10 links on the mixed path: the adjoint workload's grid."""
+    prob = synth.round_to_f32(synth.config_problem(4))
+    prob.perm = prob.perm.astype(np.float32).astype(np.float64)
+    v = synth.cotangent(prob.n, seed=synth.BASE_SEED + 4)
+    g_p_ref, g_lnk_ref = oracle.vjp(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                    prob.p, prob.pn, v)
+    with _grid(prob, "mixed") as g:
+        g.set_state(prob.p, prob.pn)
+        g_p, g_lnk = g.vjp(v)
+        g.sync_status()
+        g_p, g_lnk = g_p.cpu().numpy(), g_lnk.cpu().numpy()
+    assert _normwise(g_p, g_p_ref) <= 1e-6
+    assert _normwise(g_lnk, g_lnk_ref) <= 1e-6
+
+
+def test_autograd_fp64_against_central_differences():
+    """TPFAResidual on a 16^3 grid (FP64 path): directional derivatives of
+    v^T R in p and ln k against central differences, h = 1e-6 relative."""
+    from paper_2304_11274_gb300.api import Grid, residual
+    prob = synth.make_problem(16, 16, 16, seed=synth.BASE_SEED + 4, connectivity=10)
+    rng = np.random.default_rng(7)
+    v = torch.as_tensor(synth.cotangent(prob.n, seed=11), device="cuda")
+    with Grid(prob.nx, prob.ny, prob.nz, prob.phys, "fp64", prob.perm, prob.poro, prob.depth) as g:
+        pn = torch.as_tensor(prob.pn, device="cuda")
+        p0 = torch.as_tensor(prob.p, device="cuda")
+        g.set_state(p0, pn)
+        p = p0.clone().requires_grad_(True)
+        lk = torch.log(torch.as_tensor(prob.perm, device="cuda")).requires_grad_(True)
+        R = residual(g, p, lk)
+        (R * v).sum().backward()
+        gp, gk = p.grad.clone(), lk.grad.clone()
+
+        def f(pp, ll):
+            with torch.no_grad():
+                return float((residual(g, pp.contiguous(), ll.contiguous()) * v).sum())
+
+        for _ in range(3):
+            d = torch.as_tensor(rng.standard_normal(prob.n), device="cuda")
+            h = 1e-6 * torch.abs(p0)
+            fd = (f(p0 + h * d, lk.detach()) - f(p0 - h * d, lk.detach())) / 2.0
+            assert fd == pytest.approx(float((gp * h * d).sum()), rel=1e-5)
+            hk = 1e-6
+            fdk = (f(p0, lk.detach() + hk * d) - f(p0, lk.detach() - hk * d)) / (2 * hk)
+            assert fdk == pytest.approx(float((gk * d).sum()), rel=1e-5)
+
+
+def test_autograd_mixed_matches_oracle_gradient():
+    from paper_2304_11274_gb300.api import Grid, residual
+    prob = synth.round_to_f32(synth.make_problem(16, 16, 16, seed=synth.BASE_SEED + 4, connectivity=10))
+    prob.perm = prob.perm.astype(np.float32).astype(np.float64)
+    v = synth.cotangent(prob.n, seed=11)
+    g_p_ref, g_lnk_ref = oracle.vjp(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                    prob.p, prob.pn, v)
+    with Grid(prob.nx, prob.ny, prob.nz, prob.phys, "mixed", prob.perm, prob.poro, prob.depth) as g:
+        pn = torch.as_tensor(prob.pn, device="cuda", dtype=torch.float32)
+        p = torch.as_tensor(prob.p, device="cuda", dtype=torch.float32)
+        g.set_state(p, pn)
+        p = p.clone().requires_grad_(True)
+        lk = torch.log(torch.as_tensor(prob.perm, device="cuda")).requires_grad_(True)
+        R = residual(g, p, lk)
+        (R * torch.as_tensor(v, device="cuda")).sum().backward()
+        assert _normwise(lk.grad.cpu().numpy(), g_lnk_ref) <= 1e-6
+        # p.grad is returned in p's dtype (FP32)
+        assert _normwise(p.grad.double().cpu().numpy(), g_p_ref) <= 1e-6
