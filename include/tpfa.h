@@ -208,6 +208,63 @@ int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* str
  */
 int tpfa_sync_status(tpfa_handle h, void* stream);
 
+/* ---------------------------------------------------------------- tiling */
+
+/*
+ * Tiling of the assembly kernel: a warp marches along y over
+ * `rows_per_march` rows of a 32-cell x-segment, and a block stacks
+ * `warps_per_block` (4 or 8) consecutive z-planes.  Results do not depend on
+ * the tiling (every row is summed in the same order); only speed does.
+ */
+int tpfa_set_tiling(tpfa_handle h, int rows_per_march, int warps_per_block);
+int tpfa_get_tiling(tpfa_handle h, int* rows_per_march, int* warps_per_block);
+
+/*
+ * Choose the tiling by timing candidates (rows_per_march 16, 32, 64 x
+ * warps_per_block 4, 8) on this grid at its bound state, or take it from
+ * `cache_path` (a text file of "key rows warps" lines, key = device, path,
+ * connectivity, porosity law and log2 of the cell count); a new choice is
+ * written back.  cache_path may be NULL (no cache).  Allocates and frees
+ * temporary outputs on `stream` and synchronises it.
+ */
+int tpfa_autotune(tpfa_handle h, const char* cache_path, void* stream);
+
+/* ---------------------------------------------------------------- ensembles */
+
+typedef struct tpfa_ensemble_s* tpfa_ensemble; /* opaque, library-owned */
+
+/*
+ * An ensemble of M grids of uneven sizes (for example geomodel realisations of
+ * an uncertainty sweep) assembled by ONE persistent kernel launch, captured
+ * with the reset of its tile counter in a CUDA graph.  All grids must use
+ * TPFA_MIXED, the same connectivity, and either all c_r == 0 or all c_r != 0.
+ * The grids are BORROWED (they must outlive the ensemble); each one's bound
+ * state (tpfa_set_state / tpfa_set_pressure) is read at every batch call.
+ * Each model's residual and Jacobian are bit-identical to its own
+ * tpfa_assemble_jacobian call.
+ */
+int tpfa_create_ensemble(tpfa_ensemble* out, int M, const tpfa_handle* grids);
+
+/* Outputs of model m, as in tpfa_assemble_jacobian (vals non-NULL; R and
+ * diag64 may be NULL).  Device pointers, caller-owned. */
+int tpfa_ensemble_set_outputs(tpfa_ensemble e, int m, double* R_dev, void* vals_dev, double* diag64_dev);
+
+/* Assemble every model: uploads the model table when a bound state or an
+ * output changed since the last call, then launches the graph on `stream`. */
+int tpfa_assemble_batch(tpfa_ensemble e, void* stream);
+
+/* The ensemble's tiling (see tpfa_set_tiling), its number of tiles and of
+ * persistent blocks (the latter known after the first batch call). */
+int tpfa_ensemble_tiling(tpfa_ensemble e, int* rows_per_march, int* warps_per_block, long long* tiles,
+                         int* blocks);
+
+/* Choose the ensemble's tiling by timing the batch call (or from the cache,
+ * as tpfa_autotune).  Needs every model's state and outputs; synchronises. */
+int tpfa_ensemble_autotune(tpfa_ensemble e, const char* cache_path, void* stream);
+
+/* Free the ensemble (not its grids); NULL-safe.  Synchronises the device. */
+int tpfa_destroy_ensemble(tpfa_ensemble e);
+
 /* Size of the fixed device workspace of tpfa_assemble_jacobian_static. */
 #define TPFA_STATIC_WORKSPACE_BYTES (64ULL * 1024ULL * 1024ULL)
 

@@ -67,6 +67,15 @@ SIGNATURES = [
     ("tpfa_grid_info", _I, [_VP] + [ctypes.POINTER(_I)] * 4 + [ctypes.POINTER(_LL), ctypes.POINTER(_I)]),
     ("tpfa_get_transmissibility", _I, [_VP, _I, _VP, _VP]),
     ("tpfa_sync_status", _I, [_VP, _VP]),
+    ("tpfa_set_tiling", _I, [_VP, _I, _I]),
+    ("tpfa_get_tiling", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("tpfa_autotune", _I, [_VP, ctypes.c_char_p, _VP]),
+    ("tpfa_create_ensemble", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)]),
+    ("tpfa_ensemble_set_outputs", _I, [_VP, _I, _VP, _VP, _VP]),
+    ("tpfa_assemble_batch", _I, [_VP, _VP]),
+    ("tpfa_ensemble_tiling", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL), ctypes.POINTER(_I)]),
+    ("tpfa_ensemble_autotune", _I, [_VP, ctypes.c_char_p, _VP]),
+    ("tpfa_destroy_ensemble", _I, [_VP]),
     ("tpfa_assemble_jacobian_static", _I, [_I, _I, _I, ctypes.POINTER(TPFAParams), _I] + [_VP] * 10),
     ("tpfa_destroy", _I, [_VP]),
     ("tpfa_last_error_string", ctypes.c_char_p, []),

@@ -175,6 +175,82 @@ class Grid:
     def sync_status(self, stream=None):
         check(self.lib.tpfa_sync_status(self.handle, _stream(stream)))
 
+    # -- tiling
+    def tiling(self):
+        jy, w = ctypes.c_int(), ctypes.c_int()
+        check(self.lib.tpfa_get_tiling(self.handle, ctypes.byref(jy), ctypes.byref(w)))
+        return jy.value, w.value
+
+    def set_tiling(self, rows_per_march, warps_per_block):
+        check(self.lib.tpfa_set_tiling(self.handle, int(rows_per_march), int(warps_per_block)))
+
+    def autotune(self, cache_path=None, stream=None):
+        """Pick the tiling by timing (or from the cache file); returns it."""
+        path = cache_path.encode() if cache_path else None
+        check(self.lib.tpfa_autotune(self.handle, path, _stream(stream)))
+        return self.tiling()
+
+
+class Ensemble:
+    """Grids of uneven sizes assembled by one persistent, graph-captured launch.
+
+    The grids (mixed path, same connectivity) are borrowed; keep them alive.
+    Each model's outputs are bit-identical to its own Grid.assemble_jacobian."""
+
+    def __init__(self, grids):
+        self.lib = _capi.load()
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.handle.value for g in self.grids])
+        h = ctypes.c_void_p()
+        check(self.lib.tpfa_create_ensemble(ctypes.byref(h), len(self.grids), arr))
+        self.handle = h
+        self._outs = [None] * len(self.grids)
+
+    def set_outputs(self, m, R, vals, diag):
+        check(self.lib.tpfa_ensemble_set_outputs(self.handle, int(m), _ptr(R), _ptr(vals), _ptr(diag)))
+        self._outs[m] = (R, vals, diag)
+
+    def allocate_outputs(self):
+        """Allocate and bind (R, vals, diag64) for every model; returns them."""
+        outs = []
+        for m, g in enumerate(self.grids):
+            R, vals, diag = g.empty_outputs()
+            self.set_outputs(m, R, vals, diag)
+            outs.append((R, vals, diag))
+        return outs
+
+    def assemble(self, stream=None):
+        check(self.lib.tpfa_assemble_batch(self.handle, _stream(stream)))
+
+    def tiling(self):
+        jy, w, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        tiles = ctypes.c_longlong()
+        check(self.lib.tpfa_ensemble_tiling(self.handle, ctypes.byref(jy), ctypes.byref(w), ctypes.byref(tiles),
+                                            ctypes.byref(b)))
+        return {"rows_per_march": jy.value, "warps_per_block": w.value, "tiles": tiles.value, "blocks": b.value}
+
+    def autotune(self, cache_path=None, stream=None):
+        path = cache_path.encode() if cache_path else None
+        check(self.lib.tpfa_ensemble_autotune(self.handle, path, _stream(stream)))
+        return self.tiling()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.tpfa_destroy_ensemble(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
 
 class TPFAResidual(torch.autograd.Function):
     """R(p, ln k) of Eq. vk on a Grid whose previous-step state is bound.
@@ -216,4 +292,4 @@ def residual(grid, p, log_k):
     return TPFAResidual.apply(grid, p, log_k)
 
 
-__all__ = ["Grid", "TPFAError", "PRECISIONS", "TPFAResidual", "residual"]
+__all__ = ["Grid", "Ensemble", "TPFAError", "PRECISIONS", "TPFAResidual", "residual"]

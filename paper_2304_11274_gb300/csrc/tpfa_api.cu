@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 
 #include "tpfa_common.cuh"
@@ -98,7 +99,8 @@ struct tpfa_grid {
     const void* p = nullptr;
     const void* pn = nullptr;
     bool has_state = false;
-    int JY = 32;
+    int JY = 32;  // rows per warp march (tpfa_autotune may change it)
+    int W = 4;    // warps (z-planes) per block
     // buffers of the host-memory entry point, allocated on first use
     void* h_p = nullptr;
     double* h_R = nullptr;
@@ -163,10 +165,10 @@ int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, 
     cudaError_t e;
     if (h->prec == TPFA_MIXED) {
         AsmOut<float> o{R, static_cast<float*>(vals), diag64, h->status};
-        e = launch_assemble_mixed(kern, h->geom, h->qf, h->crk, fields_of<float>(h), o, h->JY, st);
+        e = launch_assemble_mixed(kern, h->geom, h->qf, h->crk, fields_of<float>(h), o, h->JY, h->W, st);
     } else {
         AsmOut<double> o{R, static_cast<double*>(vals), nullptr, h->status};
-        e = launch_assemble_fp64(kern, h->geom, h->qd, h->crk, fields_of<double>(h), o, h->JY, st);
+        e = launch_assemble_fp64(kern, h->geom, h->qd, h->crk, fields_of<double>(h), o, h->JY, h->W, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "assembly launch");
     return TPFA_OK;
@@ -491,6 +493,399 @@ int tpfa_destroy(tpfa_handle h) {
         h->release();
     }
     delete h;
+    return TPFA_OK;
+}
+
+}  // extern "C"
+
+// ===================================================================== tiling, autotuning, ensembles
+
+#include <stdint.h>
+
+#include <map>
+#include <vector>
+
+#include "tpfa_batch.h"
+
+namespace {
+
+// Autotune cache: a text file of "key JY W" lines (a header line starts with '#').
+std::map<std::string, std::pair<int, int>> cache_read(const char* path) {
+    std::map<std::string, std::pair<int, int>> m;
+    if (!path) return m;
+    FILE* fp = fopen(path, "r");
+    if (!fp) return m;
+    char key[256];
+    int jy, w;
+    char line[512];
+    while (fgets(line, sizeof line, fp)) {
+        if (line[0] == '#') continue;
+        if (sscanf(line, "%255s %d %d", key, &jy, &w) == 3 && jy >= 1 && (w == 4 || w == 8)) m[key] = {jy, w};
+    }
+    fclose(fp);
+    return m;
+}
+
+bool cache_write(const char* path, const std::map<std::string, std::pair<int, int>>& m) {
+    if (!path) return true;
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* fp = fopen(tmp.c_str(), "w");
+    if (!fp) return false;
+    fprintf(fp, "# tpfa autotune cache v1: key rows_per_march warps_per_block\n");
+    for (const auto& kv : m) fprintf(fp, "%s %d %d\n", kv.first.c_str(), kv.second.first, kv.second.second);
+    fclose(fp);
+    return rename(tmp.c_str(), path) == 0;
+}
+
+std::string device_tag(int dev) {
+    int maj = 0, mnr = 0;
+    cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev);
+    char b[32];
+    snprintf(b, sizeof b, "sm%d%d", maj, mnr);
+    return b;
+}
+
+int log2_bucket(long long n) {
+    int b = 0;
+    while ((1LL << (b + 1)) <= n) ++b;
+    return b;
+}
+
+const int kTuneJY[] = {16, 32, 64};
+const int kTuneW[] = {4, 8};
+
+}  // namespace
+
+struct tpfa_ensemble_s {
+    int device = 0;
+    int M = 0;
+    std::vector<tpfa_handle> grids;
+    bool diag = false, crk = false;
+    std::vector<double*> R;
+    std::vector<float*> vals;
+    std::vector<double*> diag64;
+    BatchModel* d_models = nullptr;
+    BatchModel* h_stage = nullptr;  // pinned upload buffer
+    std::vector<BatchModel> last;   // the table last uploaded
+    cudaEvent_t upload_done = nullptr;
+    unsigned long long* ticket = nullptr;
+    long long total = 0;
+    int JY = 32, W = 4;
+    int blocks = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // parameters the graph's kernel node was built with
+    int g_JY = 0, g_W = 0, g_blocks = 0;
+    long long g_total = -1;
+
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (upload_done) cudaEventDestroy(upload_done);
+        dev_free(d_models);
+        dev_free(ticket);
+        if (h_stage) cudaFreeHost(h_stage);
+        exec = nullptr, graph = nullptr, upload_done = nullptr, d_models = nullptr, ticket = nullptr, h_stage = nullptr;
+    }
+};
+
+namespace {
+
+int build_table(tpfa_ensemble e, std::vector<BatchModel>& tab) {
+    tab.resize(e->M);
+    long long first = 0;
+    for (int m = 0; m < e->M; ++m) {
+        tpfa_grid* h = e->grids[m];
+        if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "ensemble model %d has no state (tpfa_set_state)", m);
+        if (!e->vals[m]) return fail(TPFA_ERR_INVALID_ARG, "ensemble model %d has no outputs (tpfa_ensemble_set_outputs)", m);
+        BatchModel bm;
+        memset(&bm, 0, sizeof bm);
+        bm.g = h->geom;
+        bm.q = h->qf;
+        bm.f = fields_of<float>(h);
+        bm.o = AsmOut<float>{e->R[m], e->vals[m], e->diag64[m], h->status};
+        bm.tx = (h->nx + 31) / 32;
+        bm.ty = (h->ny + e->JY - 1) / e->JY;
+        bm.tz = (h->nz + e->W - 1) / e->W;
+        bm.crk = h->crk ? 1 : 0;
+        bm.first = first;
+        first += (long long)bm.tx * bm.ty * bm.tz;
+        tab[m] = bm;
+    }
+    e->total = first;
+    return TPFA_OK;
+}
+
+int ensure_graph(tpfa_ensemble e) {
+    int bps = 0;
+    cudaError_t ce = batch_blocks_per_sm(e->diag, e->crk, e->W, &bps);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ensemble kernel occupancy");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
+    e->blocks = (int)std::min<long long>((long long)sms * (bps > 0 ? bps : 1), e->total > 0 ? e->total : 1);
+    if (e->exec && e->g_JY == e->JY && e->g_W == e->W && e->g_total == e->total && e->g_blocks == e->blocks)
+        return TPFA_OK;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    e->exec = nullptr;
+    e->graph = nullptr;
+    const void* func = nullptr;
+    int smem = 0;
+    ce = batch_kernel(e->diag, e->crk, e->W, &func, &smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ensemble kernel");
+    ce = cudaGraphCreate(&e->graph, 0);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphCreate");
+    // node 1: reset the tile ticket; node 2: the persistent kernel
+    cudaMemsetParams mp;
+    memset(&mp, 0, sizeof mp);
+    mp.dst = e->ticket;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 2;
+    mp.height = 1;
+    cudaGraphNode_t n_reset, n_kernel;
+    ce = cudaGraphAddMemsetNode(&n_reset, e->graph, nullptr, 0, &mp);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph memset node");
+    const BatchModel* models = e->d_models;
+    int M = e->M;
+    long long total = e->total;
+    int JY = e->JY;
+    unsigned long long* ticket = e->ticket;
+    void* args[] = {&models, &M, &total, &JY, &ticket};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void*>(func);
+    kp.gridDim = dim3(e->blocks, 1, 1);
+    kp.blockDim = dim3(32, e->W, 1);
+    kp.sharedMemBytes = smem;
+    kp.kernelParams = args;
+    ce = cudaGraphAddKernelNode(&n_kernel, e->graph, &n_reset, 1, &kp);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph kernel node");
+    ce = cudaGraphInstantiate(&e->exec, e->graph, 0);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+    e->g_JY = e->JY, e->g_W = e->W, e->g_total = e->total, e->g_blocks = e->blocks;
+    return TPFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tpfa_set_tiling(tpfa_handle h, int rows_per_march, int warps_per_block) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (rows_per_march < 1 || (warps_per_block != 4 && warps_per_block != 8))
+        return fail(TPFA_ERR_INVALID_ARG, "rows_per_march must be >= 1 and warps_per_block 4 or 8");
+    h->JY = rows_per_march;
+    h->W = warps_per_block;
+    return TPFA_OK;
+}
+
+int tpfa_get_tiling(tpfa_handle h, int* rows_per_march, int* warps_per_block) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (rows_per_march) *rows_per_march = h->JY;
+    if (warps_per_block) *warps_per_block = h->W;
+    return TPFA_OK;
+}
+
+int tpfa_autotune(tpfa_handle h, const char* cache_path, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    DeviceGuard dg(h->device);
+    char key[256];
+    snprintf(key, sizeof key, "grid/%s/%s/c%d/r%d/n%d", device_tag(h->device).c_str(),
+             h->prec == TPFA_MIXED ? "mixed" : "fp64", h->prm.connectivity, h->crk ? 1 : 0, log2_bucket(h->N));
+    auto cache = cache_read(cache_path);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        h->JY = it->second.first;
+        h->W = it->second.second;
+        return TPFA_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *R = nullptr, *vals = nullptr, *diag = nullptr;
+    cudaError_t e = cudaMallocAsync(&R, sizeof(double) * (size_t)h->N, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&vals, h->real_size * (size_t)h->nnz, st);
+    if (e == cudaSuccess && h->prec == TPFA_MIXED) e = cudaMallocAsync(&diag, sizeof(double) * (size_t)h->N, st);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float best = 1e30f;
+    int bj = h->JY, bw = h->W;
+    for (int jy : kTuneJY) {
+        for (int w : kTuneW) {
+            if (e != cudaSuccess) break;
+            h->JY = jy;
+            h->W = w;
+            for (int r = 0; r < 2 && !rc; ++r) rc = launch(h, AsmKernel::YMarch, (double*)R, vals, (double*)diag, st);
+            if (rc) break;
+            cudaEventRecord(a, st);
+            for (int r = 0; r < 3 && !rc; ++r) rc = launch(h, AsmKernel::YMarch, (double*)R, vals, (double*)diag, st);
+            cudaEventRecord(b, st);
+            e = cudaEventSynchronize(b);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && ms < best) best = ms, bj = jy, bw = w;
+        }
+        if (rc) break;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (R) cudaFreeAsync(R, st);
+    if (vals) cudaFreeAsync(vals, st);
+    if (diag) cudaFreeAsync(diag, st);
+    cudaStreamSynchronize(st);
+    h->JY = bj;
+    h->W = bw;
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    cache[key] = {bj, bw};
+    if (!cache_write(cache_path, cache)) return fail(TPFA_ERR_INVALID_ARG, "cannot write autotune cache %s", cache_path);
+    return TPFA_OK;
+}
+
+int tpfa_create_ensemble(tpfa_ensemble* out, int M, const tpfa_handle* grids) {
+    if (!out) return fail(TPFA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (M < 1 || !grids) return fail(TPFA_ERR_INVALID_ARG, "an ensemble needs M >= 1 grids");
+    for (int m = 0; m < M; ++m) {
+        if (!grids[m]) return fail(TPFA_ERR_INVALID_ARG, "grid %d is NULL", m);
+        if (grids[m]->prec != TPFA_MIXED) return fail(TPFA_ERR_INVALID_ARG, "ensembles use the mixed path (grid %d is FP64)", m);
+        if (grids[m]->geom.diag != grids[0]->geom.diag || grids[m]->crk != grids[0]->crk)
+            return fail(TPFA_ERR_INVALID_ARG, "grid %d differs from grid 0 in connectivity or in c_r == 0", m);
+        if (grids[m]->device != grids[0]->device) return fail(TPFA_ERR_INVALID_ARG, "grid %d is on another device", m);
+    }
+    tpfa_ensemble e = new tpfa_ensemble_s();
+    e->device = grids[0]->device;
+    e->M = M;
+    e->grids.assign(grids, grids + M);
+    e->diag = grids[0]->geom.diag != 0;
+    e->crk = grids[0]->crk;
+    e->R.assign(M, nullptr);
+    e->vals.assign(M, nullptr);
+    e->diag64.assign(M, nullptr);
+    DeviceGuard dg(e->device);
+    void* dm = nullptr;
+    void* tk = nullptr;
+    cudaError_t ce = dev_alloc(&dm, sizeof(BatchModel) * (size_t)M);
+    if (ce == cudaSuccess) ce = dev_alloc(&tk, sizeof(unsigned long long));
+    e->d_models = (BatchModel*)dm;
+    e->ticket = (unsigned long long*)tk;
+    if (ce == cudaSuccess && !alloc_fault_injected()) ce = cudaMallocHost((void**)&e->h_stage, sizeof(BatchModel) * (size_t)M);
+    else if (ce == cudaSuccess) ce = cudaErrorMemoryAllocation;
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->upload_done, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        e->release();
+        delete e;
+        return fail(TPFA_ERR_OOM, "ensemble allocation failed");
+    }
+    *out = e;
+    return TPFA_OK;
+}
+
+int tpfa_ensemble_set_outputs(tpfa_ensemble e, int m, double* R_dev, void* vals_dev, double* diag64_dev) {
+    if (!e) return fail(TPFA_ERR_INVALID_ARG, "ensemble is NULL");
+    if (m < 0 || m >= e->M) return fail(TPFA_ERR_INVALID_ARG, "model index %d out of range", m);
+    if (!vals_dev) return fail(TPFA_ERR_INVALID_ARG, "vals must be non-NULL");
+    e->R[m] = R_dev;
+    e->vals[m] = static_cast<float*>(vals_dev);
+    e->diag64[m] = diag64_dev;
+    return TPFA_OK;
+}
+
+int tpfa_assemble_batch(tpfa_ensemble e, void* stream) {
+    if (!e) return fail(TPFA_ERR_INVALID_ARG, "ensemble is NULL");
+    DeviceGuard dg(e->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<BatchModel> tab;
+    int rc = build_table(e, tab);
+    if (rc) return rc;
+    if (e->last.size() != tab.size() || memcmp(e->last.data(), tab.data(), sizeof(BatchModel) * tab.size()) != 0) {
+        cudaError_t ce = cudaEventSynchronize(e->upload_done);  // the staging buffer is free again
+        if (ce == cudaSuccess) {
+            memcpy(e->h_stage, tab.data(), sizeof(BatchModel) * tab.size());
+            ce = cudaMemcpyAsync(e->d_models, e->h_stage, sizeof(BatchModel) * tab.size(), cudaMemcpyHostToDevice, st);
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(e->upload_done, st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ensemble table upload");
+        e->last = tab;
+    }
+    rc = ensure_graph(e);
+    if (rc) return rc;
+    cudaError_t ce = cudaGraphLaunch(e->exec, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphLaunch");
+    return TPFA_OK;
+}
+
+int tpfa_ensemble_tiling(tpfa_ensemble e, int* rows_per_march, int* warps_per_block, long long* tiles, int* blocks) {
+    if (!e) return fail(TPFA_ERR_INVALID_ARG, "ensemble is NULL");
+    if (rows_per_march) *rows_per_march = e->JY;
+    if (warps_per_block) *warps_per_block = e->W;
+    if (tiles) *tiles = e->total;
+    if (blocks) *blocks = e->blocks;
+    return TPFA_OK;
+}
+
+int tpfa_ensemble_autotune(tpfa_ensemble e, const char* cache_path, void* stream) {
+    if (!e) return fail(TPFA_ERR_INVALID_ARG, "ensemble is NULL");
+    DeviceGuard dg(e->device);
+    long long cells = 0;
+    for (auto h : e->grids) cells += h->N;
+    char key[256];
+    snprintf(key, sizeof key, "ensemble/%s/M%d/c%d/r%d/n%d", device_tag(e->device).c_str(), e->M,
+             e->diag ? 10 : 6, e->crk ? 1 : 0, log2_bucket(cells));
+    auto cache = cache_read(cache_path);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        e->JY = it->second.first;
+        e->W = it->second.second;
+        return TPFA_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t ce = cudaEventCreate(&a);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&b);
+    float best = 1e30f;
+    int bj = e->JY, bw = e->W, rc = TPFA_OK;
+    for (int jy : kTuneJY) {
+        for (int w : kTuneW) {
+            if (ce != cudaSuccess || rc) break;
+            e->JY = jy;
+            e->W = w;
+            rc = tpfa_assemble_batch(e, stream);
+            if (rc) break;
+            cudaEventRecord(a, st);
+            for (int r = 0; r < 3 && !rc; ++r) rc = tpfa_assemble_batch(e, stream);
+            cudaEventRecord(b, st);
+            ce = cudaEventSynchronize(b);
+            float ms = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, b);
+            if (ce == cudaSuccess && ms < best) best = ms, bj = jy, bw = w;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    e->JY = bj;
+    e->W = bw;
+    if (rc) return rc;
+    if (ce != cudaSuccess) return cuda_fail(ce, "ensemble autotune");
+    cache[key] = {bj, bw};
+    if (!cache_write(cache_path, cache)) return fail(TPFA_ERR_INVALID_ARG, "cannot write autotune cache %s", cache_path);
+    return TPFA_OK;
+}
+
+int tpfa_destroy_ensemble(tpfa_ensemble e) {
+    if (!e) return TPFA_OK;
+    {
+        DeviceGuard dg(e->device);
+        cudaDeviceSynchronize();
+        e->release();
+    }
+    delete e;
     return TPFA_OK;
 }
 

@@ -79,11 +79,9 @@ static cudaError_t launch_naive_t(const GridGeom& g, const typename PhysOf<Real>
     return cudaGetLastError();
 }
 
-template <typename Real, bool DIAG, bool CRK, bool JAC>
-static cudaError_t launch_ymarch_t(const GridGeom& g, const typename PhysOf<Real>::type& q,
-                                   const AsmFields<Real>& f, const AsmOut<Real>& o, int JY,
-                                   cudaStream_t st) {
-    constexpr int W = 4;
+template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
+static cudaError_t launch_ymarch_w(const GridGeom& g, const typename PhysOf<Real>::type& q,
+                                   const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, cudaStream_t st) {
     constexpr int smem = ymarch_smem_bytes<Real, W>();
     static bool attr_set = false;  // per instantiation; the attribute is per function
     if (!attr_set) {
@@ -98,9 +96,17 @@ static cudaError_t launch_ymarch_t(const GridGeom& g, const typename PhysOf<Real
     return cudaGetLastError();
 }
 
+template <typename Real, bool DIAG, bool CRK, bool JAC>
+static cudaError_t launch_ymarch_t(const GridGeom& g, const typename PhysOf<Real>::type& q,
+                                   const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int W,
+                                   cudaStream_t st) {
+    if (W == 8) return launch_ymarch_w<Real, DIAG, CRK, JAC, 8>(g, q, f, o, JY, st);
+    return launch_ymarch_w<Real, DIAG, CRK, JAC, 4>(g, q, f, o, JY, st);
+}
+
 template <typename Real>
 static cudaError_t dispatch(AsmKernel kern, const GridGeom& g, const typename PhysOf<Real>::type& q,
-                            bool crk, const AsmFields<Real>& f, const AsmOut<Real>& o, int JY,
+                            bool crk, const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int W,
                             cudaStream_t st) {
     const bool jac = o.vals != nullptr;
     if (kern == AsmKernel::Naive) {
@@ -108,27 +114,27 @@ static cudaError_t dispatch(AsmKernel kern, const GridGeom& g, const typename Ph
         return jac ? launch_naive_t<Real, false, true>(g, q, f, o, st) : launch_naive_t<Real, false, false>(g, q, f, o, st);
     }
     if (g.diag) {
-        if (crk) return jac ? launch_ymarch_t<Real, true, true, true>(g, q, f, o, JY, st)
-                            : launch_ymarch_t<Real, true, true, false>(g, q, f, o, JY, st);
-        return jac ? launch_ymarch_t<Real, true, false, true>(g, q, f, o, JY, st)
-                   : launch_ymarch_t<Real, true, false, false>(g, q, f, o, JY, st);
+        if (crk) return jac ? launch_ymarch_t<Real, true, true, true>(g, q, f, o, JY, W, st)
+                            : launch_ymarch_t<Real, true, true, false>(g, q, f, o, JY, W, st);
+        return jac ? launch_ymarch_t<Real, true, false, true>(g, q, f, o, JY, W, st)
+                   : launch_ymarch_t<Real, true, false, false>(g, q, f, o, JY, W, st);
     }
-    if (crk) return jac ? launch_ymarch_t<Real, false, true, true>(g, q, f, o, JY, st)
-                        : launch_ymarch_t<Real, false, true, false>(g, q, f, o, JY, st);
-    return jac ? launch_ymarch_t<Real, false, false, true>(g, q, f, o, JY, st)
-               : launch_ymarch_t<Real, false, false, false>(g, q, f, o, JY, st);
+    if (crk) return jac ? launch_ymarch_t<Real, false, true, true>(g, q, f, o, JY, W, st)
+                        : launch_ymarch_t<Real, false, true, false>(g, q, f, o, JY, W, st);
+    return jac ? launch_ymarch_t<Real, false, false, true>(g, q, f, o, JY, W, st)
+               : launch_ymarch_t<Real, false, false, false>(g, q, f, o, JY, W, st);
 }
 
 cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk,
-                                  const AsmFields<float>& f, const AsmOut<float>& o, int JY,
+                                  const AsmFields<float>& f, const AsmOut<float>& o, int JY, int W,
                                   cudaStream_t st) {
-    return dispatch<float>(kern, g, q, crk, f, o, JY, st);
+    return dispatch<float>(kern, g, q, crk, f, o, JY, W, st);
 }
 
 cudaError_t launch_assemble_fp64(AsmKernel kern, const GridGeom& g, const PhysD& q, bool crk,
-                                 const AsmFields<double>& f, const AsmOut<double>& o, int JY,
+                                 const AsmFields<double>& f, const AsmOut<double>& o, int JY, int W,
                                  cudaStream_t st) {
-    return dispatch<double>(kern, g, q, crk, f, o, JY, st);
+    return dispatch<double>(kern, g, q, crk, f, o, JY, W, st);
 }
 
 }  // namespace tpfa

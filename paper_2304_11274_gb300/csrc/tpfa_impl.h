@@ -13,11 +13,12 @@ struct PhysD;
 
 enum class AsmKernel { Naive, YMarch };
 
+// JY: rows per warp march; W: warps (z-planes) per block, 4 or 8.
 cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk,
-                                  const AsmFields<float>& f, const AsmOut<float>& o, int JY,
+                                  const AsmFields<float>& f, const AsmOut<float>& o, int JY, int W,
                                   cudaStream_t st);
 cudaError_t launch_assemble_fp64(AsmKernel kern, const GridGeom& g, const PhysD& q, bool crk,
-                                 const AsmFields<double>& f, const AsmOut<double>& o, int JY,
+                                 const AsmFields<double>& f, const AsmOut<double>& o, int JY, int W,
                                  cudaStream_t st);
 
 // Setup kernels (tpfa_setup.cu).

@@ -136,7 +136,7 @@ extern "C" int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_
                                (const float*)T[0], (const float*)T[1], (const float*)T[2],
                                (const float*)(T[3] ? T[3] : T[0]), (const float*)(T[4] ? T[4] : T[0])};
             AsmOut<float> o{R_dev, (float*)vals_dev, diag64_dev, status};
-            e = launch_assemble_mixed(AsmKernel::YMarch, g, q, crk, f, o, 32, st);
+            e = launch_assemble_mixed(AsmKernel::YMarch, g, q, crk, f, o, 32, 4, st);
         }
     } else {
         if (e == cudaSuccess)
@@ -149,7 +149,7 @@ extern "C" int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_
                                 (const double*)T[0], (const double*)T[1], (const double*)T[2],
                                 (const double*)(T[3] ? T[3] : T[0]), (const double*)(T[4] ? T[4] : T[0])};
             AsmOut<double> o{R_dev, (double*)vals_dev, nullptr, status};
-            e = launch_assemble_fp64(AsmKernel::YMarch, g, q, crk, f, o, 32, st);
+            e = launch_assemble_fp64(AsmKernel::YMarch, g, q, crk, f, o, 32, 4, st);
         }
     }
     if (e != cudaSuccess) return report_error(TPFA_ERR_CUDA, cudaGetErrorString(e));

@@ -435,30 +435,35 @@ struct YMarch {
     }
 };
 
+// Dynamic shared memory of one block of W warps: per warp two CSR staging
+// buffers, the RING x NF input ring and the RING m^n values.
 template <typename Real, int W>
 constexpr int ymarch_smem_bytes() {
     return W * (2 * (32 * NSLOT + 16 / (int)sizeof(Real)) * (int)sizeof(Real) +
                 3 * 18 * 32 * (int)sizeof(Real) + 3 * 32 * (int)sizeof(double));
 }
 
+// One block's work: x-segment bx, y-run by, z-block bz of one grid.  Shared
+// by the single-grid kernel and the persistent ensemble kernel (whose blocks
+// call it once per tile they claim), so both produce identical rows.
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
-__global__ void __launch_bounds__(32 * W, (sizeof(Real) == 4 ? 16 : 8) / W)
-    k_assemble_ymarch(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f, AsmOut<Real> o, int JY) {
+__device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename PhysOf<Real>::type& q,
+                                            const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int bx, int by,
+                                            int bz, unsigned char* smem) {
     using M_t = YMarch<Real, DIAG, CRK, JAC, W>;
     constexpr int BUF = 32 * NSLOT + 16 / (int)sizeof(Real);
-    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int k = blockIdx.z * W + w;
+    const int k = bz * W + w;
     if (k >= g.nz) return;  // warp-uniform
     // per warp: two staging buffers, then the input ring, then the m^n ring
     Real* stage = reinterpret_cast<Real*>(smem) + w * 2 * BUF;
     Real* ring = reinterpret_cast<Real*>(smem) + W * 2 * BUF + w * M_t::RING * M_t::NF * 32;
     double* ringm = reinterpret_cast<double*>(reinterpret_cast<Real*>(smem) + W * 2 * BUF +
                                               W * M_t::RING * M_t::NF * 32) + w * M_t::RING * 32;
-    M_t M(g, q, f, o, lane, blockIdx.x * 32, k);
+    M_t M(g, q, f, o, lane, bx * 32, k);
     M.ring = ring;
     M.ringm = ringm;
-    const int j0 = blockIdx.y * JY;
+    const int j0 = by * JY;
     const int j1 = min(j0 + JY, g.ny);
     const bool zint = M.zm && M.zp;
 
@@ -497,6 +502,13 @@ __global__ void __launch_bounds__(32 * W, (sizeof(Real) == 4 ? 16 : 8) / W)
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     M.drain();
+}
+
+template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
+__global__ void __launch_bounds__(32 * W, (sizeof(Real) == 4 ? 16 : 8) / W)
+    k_assemble_ymarch(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f, AsmOut<Real> o, int JY) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ymarch_tile<Real, DIAG, CRK, JAC, W>(g, q, f, o, JY, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 }  // namespace tpfa
