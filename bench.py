@@ -171,6 +171,7 @@ def run_ours(args):
     p_dev = [torch.as_tensor(x.astype(np.float32), device=dev) for x in pres]
     pn_dev = torch.as_tensor(prob.pn.astype(np.float32), device=dev)
     g.set_state(p_dev[0], pn_dev)
+    tiling = g.autotune(None)  # rows per march, warps per block
     R, vals, diag = g.empty_outputs()
     stream = torch.cuda.current_stream(dev)
 
@@ -275,6 +276,9 @@ def run_ours(args):
                 "note": "plain FP64 path, same grid; bound by the FP64 pipe, not HBM"}
         g64.close()
 
+    ensemble = None if (args.skip_ensemble or world > 1) else measure_ensemble(dev, stream)
+    adjoint = None if (args.skip_adjoint or world > 1) else measure_adjoint(dev, stream)
+
     line = {
         "metric": METRIC,
         "value": value,
@@ -292,7 +296,8 @@ def run_ours(args):
                    "tpfa_residual_jacobian_%dx%dx%d_10pt_mixed" % tuple(args.shape), "grid": list(args.shape), "cells": prob.n, "links_per_cell": CONN,
                    "nnz": g.nnz, "precision": "mixed: FP32 flux + Kahan residual, FP64 accumulation/diagonal/R",
                    "l2": "inputs+outputs 6.7 GB per step > 129 MB L2; no flush",
-                   "pressure_vectors": len(pres), "parallelism": f"replicas x{world}"},
+                   "pressure_vectors": len(pres), "parallelism": f"replicas x{world}",
+                   "tiling": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
                      "kernel": "k_assemble_ymarch<float,DIAG,!CR,JAC>", "kernel_source_sha256_16": khash},
@@ -300,6 +305,8 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "fp64": fp64,
+        "ensemble": ensemble,
+        "adjoint": adjoint,
     }
     if rank == 0 and world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
@@ -307,6 +314,93 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_ensemble(dev, stream, reps=10):
+    """The 64-model uneven ensemble (nx, ny ~ U{64..256}, nz ~ U{32..128},
+    10 links, mixed): one graph-captured persistent launch per step against
+    64 sequential single-grid launches, both with autotuned tiling."""
+    import torch
+
+    from paper_2304_11274_gb300 import synth
+    from paper_2304_11274_gb300.api import Ensemble, Grid
+
+    shapes = synth.ensemble_shapes()
+    grids, keep = [], []
+    for m, (nx, ny, nz) in enumerate(shapes):
+        prob = synth.make_problem(nx, ny, nz, synth.BASE_SEED + 1000 + m, connectivity=CONN)
+        g = Grid(nx, ny, nz, prob.phys, "mixed", prob.perm, prob.poro, prob.depth, device=dev)
+        p = torch.as_tensor(prob.p.astype(np.float32), device=dev)
+        pn = torch.as_tensor(prob.pn.astype(np.float32), device=dev)
+        g.set_state(p, pn)
+        keep.append((p, pn))
+        grids.append(g)
+    cells = sum(g.n for g in grids)
+    ens = Ensemble(grids)
+    outs = ens.allocate_outputs()
+    tiling = ens.autotune(None)
+    for g in grids:
+        g.autotune(None)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    batched_ms = timed(ens.assemble)
+
+    def sequential():
+        for m, g in enumerate(grids):
+            R, vals, diag = outs[m]
+            g.assemble_jacobian(R, vals, diag)
+
+    seq_ms = timed(sequential)
+    for g in grids:
+        g.sync_status()
+    info = ens.tiling()
+    ens.close()
+    for g in grids:
+        g.close()
+    return {"models": len(shapes), "cells": cells, "unit": "cells/s",
+            "batched_value": cells / (batched_ms * 1e-3), "batched_ms": batched_ms,
+            "sequential_value": cells / (seq_ms * 1e-3), "sequential_ms": seq_ms,
+            "launches_per_step": {"batched": 1, "sequential": len(shapes)},
+            "tiling": info, "note": "one CUDA-graph launch of the persistent kernel vs 64 single-grid launches"}
+
+
+def measure_adjoint(dev, stream, reps=20):
+    """Adjoint (v^T dR/dp and v^T dR/d ln k) on 128^3, 10 links, mixed."""
+    import torch
+
+    from paper_2304_11274_gb300 import synth
+    from paper_2304_11274_gb300.api import Grid
+
+    prob = synth.config_problem(4)
+    g = Grid(prob.nx, prob.ny, prob.nz, prob.phys, "mixed", prob.perm, prob.poro, prob.depth, device=dev)
+    g.set_state(torch.as_tensor(prob.p.astype(np.float32), device=dev),
+                torch.as_tensor(prob.pn.astype(np.float32), device=dev))
+    v = torch.as_tensor(synth.cotangent(prob.n, synth.BASE_SEED + 4), device=dev)
+    for _ in range(3):
+        g.vjp(v)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.vjp(v)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    g.sync_status()
+    ms = a.elapsed_time(b) / reps
+    g.close()
+    return {"grid": [prob.nx, prob.ny, prob.nz], "value": prob.n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
+            "outputs": "g_p and g_lnk (FP64)", "bound": "fp64 pipe (v-weighted sums in FP64)"}
 
 
 # ---------------------------------------------------------------------- oracle on the host
@@ -371,6 +465,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--skip-ensemble", action="store_true", help="skip the 64-model batched ensemble line")
+    ap.add_argument("--skip-adjoint", action="store_true", help="skip the adjoint (VJP) line")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
                     help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")
     args = ap.parse_args()
