@@ -121,16 +121,14 @@ struct YMarch {
 
     // ---- row inputs, prefetched into a per-warp shared-memory ring of RING
     // rows with cp.async (4- or 8-byte copies by each lane; lanes whose value
-    // does not exist copy nothing and get zeros).  Field f of row r for lane l
-    // lives at ring[slot(r) * NF * 32 + f * 32 + l].
+    // does not exist copy nothing and get zeros).  Field f of the row in ring
+    // slot s for lane l lives at ring[s * NF * 32 + f * 32 + l]; m^n at
+    // ringm[s * 32 + l].  Slots rotate explicitly (no modulo per access).
     static constexpr int RING = 3;
     enum { F_P, F_Z, F_HP, F_HZ, F_TX, F_TY, F_TZ, F_TPP, F_TMP, F_PN, F_PHI, F_PZM, F_ZZM, F_TZM, F_PZP, F_ZZP,
            F_HT1, F_HT2, NF };
     Real* ring;      // RING * NF * 32 values
     double* ringm;   // RING * 32 values of m^n
-
-    // Ring slot of row r (r >= -1: the march starts one row above its first row).
-    static __device__ __forceinline__ int slot(int r) { return (r + RING) % RING; }
 
     __device__ __forceinline__ void cp4(Real* dst, const Real* src, bool valid) const {
         const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -144,9 +142,10 @@ struct YMarch {
         const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
     }
-    // Request every input of row r (a row outside the grid requests nothing).
-    __device__ __forceinline__ void issue_row(int r) const {
-        Real* R = ring + slot(r) * (NF * 32) + lane;
+    // Request every input of row r into ring slot sl (a row outside the grid
+    // requests nothing).
+    __device__ __forceinline__ void issue_row(int r, int sl) const {
+        Real* R = ring + sl * (NF * 32) + lane;
         const bool rv = r >= 0 && r < ny;
         const int c = kb + nx * (rv ? r : 0) + (act ? i : 0);
         const bool a = rv && act;
@@ -175,15 +174,16 @@ struct YMarch {
             const bool h2l = h1 && r > 0, h2r = rv && lane == 31 && hact && r > 0;
             cp4(R + F_HT2 * 32, h2l ? f.Tpp + (c - nx - 1) : f.Tmp + (h2r ? c - nx + 1 : c), h2l || h2r);
         }
-        cp8(ringm + slot(r) * 32 + lane, f.mn + c, a);
+        cp8(ringm + sl * 32 + lane, f.mn + c, a);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    // Wait until every requested row but the most recent one has arrived.
+    // Wait until every requested row but the most recent one has arrived
+    // (each lane reads back only what it copied itself).
     __device__ __forceinline__ void wait_all_but_newest() const {
         asm volatile("cp.async.wait_group 1;" ::: "memory");
     }
-    __device__ __forceinline__ YIn<Real> read_in(int r) const {
-        const Real* R = ring + slot(r) * (NF * 32) + lane;
+    __device__ __forceinline__ YIn<Real> read_in(int sl) const {
+        const Real* R = ring + sl * (NF * 32) + lane;
         YIn<Real> D;
         D.Tx = R[F_TX * 32];
         D.Ty = R[F_TY * 32];
@@ -192,7 +192,7 @@ struct YMarch {
         D.Tmp = DIAG ? R[F_TMP * 32] : Real(0);
         D.pn = R[F_PN * 32];
         D.phi0 = CRK ? R[F_PHI * 32] : Real(0);
-        D.mn = ringm[slot(r) * 32 + lane];
+        D.mn = ringm[sl * 32 + lane];
         D.p_zm = R[F_PZM * 32];
         D.z_zm = R[F_ZZM * 32];
         D.Tz_m = R[F_TZM * 32];
@@ -202,8 +202,8 @@ struct YMarch {
         D.hT2 = DIAG ? R[F_HT2 * 32] : Real(0);
         return D;
     }
-    __device__ __forceinline__ YRow<Real> row_cells(int r) const {
-        const Real* R = ring + slot(r) * (NF * 32) + lane;
+    __device__ __forceinline__ YRow<Real> row_cells(int sl) const {
+        const Real* R = ring + sl * (NF * 32) + lane;
         return make_row(R[F_P * 32], R[F_Z * 32], R[F_HP * 32], R[F_HZ * 32]);
     }
 
@@ -467,28 +467,34 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
     const int j1 = min(j0 + JY, g.ny);
     const bool zint = M.zm && M.zp;
 
-    // prologue: rows j0-1 and j0 (cells, and the links of row j0-1 into row j0)
-    M.issue_row(j0 - 1);
-    M.issue_row(j0);
-    M.issue_row(j0 + 1);
+    // prologue: rows j0-1, j0, j0+1 into ring slots 0, 1, 2; cells of rows
+    // j0-1 and j0 and the links of row j0-1 into row j0 (unused when j0 == 0)
+    M.issue_row(j0 - 1, 0);
+    M.issue_row(j0, 1);
+    M.issue_row(j0 + 1, 2);
     M.wait_all_but_newest();
-    YRow<Real> P = M.row_cells(j0 - 1);
-    YRow<Real> C = M.row_cells(j0);
+    YRow<Real> P = M.row_cells(0);
+    YRow<Real> C = M.row_cells(1);
     Real Ty_prev, Tpp_prev, Tmp_prev;
     {
-        const YIn<Real> Dp = M.read_in(j0 - 1);  // zeros when j0 == 0
+        const YIn<Real> Dp = M.read_in(0);
         Ty_prev = Dp.Ty;
         Tpp_prev = Dp.Tpp;
         Tmp_prev = Dp.Tmp;
     }
     YUp<Real> U = M.up_links(P, C, Ty_prev, Tpp_prev, Tmp_prev);
+    int s0 = 1, s1 = 2, s2 = 0;  // ring slots of rows j, j+1, j+2
 
     for (int j = j0; j < j1; ++j) {
         // row j+2 is requested now and used two steps later; row j+1 arrived
-        M.issue_row(j + 2);
+        M.issue_row(j + 2, s2);
         M.wait_all_but_newest();
-        const YRow<Real> N = M.row_cells(j + 1);
-        const YIn<Real> D = M.read_in(j);
+        const YRow<Real> N = M.row_cells(s1);
+        const YIn<Real> D = M.read_in(s0);
+        const int st = s0;
+        s0 = s1;
+        s1 = s2;
+        s2 = st;
         Real* buf = stage + ((j - j0) & 1) * BUF;
         M.buffer_ready();
         const bool full = M.xint && zint && j > 0 && j + 1 < M.ny;

@@ -84,11 +84,12 @@ def test_parity_vs_oracle(shape, conn, precision, c_r):
         assert np.allclose(out["vals"][d].astype(np.float64), out["diag"], rtol=2 * C.EPS32, atol=0)
 
 
+@pytest.mark.parametrize("shape", [(70, 41, 11), (72, 41, 11)])  # per-lane and 16-byte-chunk input paths
 @pytest.mark.parametrize("conn", [6, 10])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("c_r", [0.0, 1e-9])
-def test_kernel_variants_bit_identical(conn, precision, c_r):
-    prob = problem((70, 41, 11), conn, precision, c_r=c_r, seed=3)
+def test_kernel_variants_bit_identical(shape, conn, precision, c_r):
+    prob = problem(shape, conn, precision, c_r=c_r, seed=3)
     a = run_gpu(prob, precision, "naive")
     b = run_gpu(prob, precision, "tiled")
     assert np.array_equal(a["R"].view(np.uint64), b["R"].view(np.uint64))
