@@ -38,16 +38,17 @@ METRIC = "cells/s for TPFA residual+Jacobian (1 GB300) and % of HBM roofline, mi
 SHAPE = (512, 512, 256)
 CONN = 10
 WORKLOAD = "tpfa_residual_jacobian_512x512x256_10pt_mixed"
-KERNEL_SOURCES = ["tpfa_assemble.cu", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
+KERNEL_SOURCES = ["tpfa_assemble.cu", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
+JVP_SOURCES = ["tpfa_jvp.cu", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
 
 
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2304_11274_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -62,10 +63,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel_hash: str):
+def profiled_traffic(kernel_hash: str, summary="assemble_mixed_512x512x256.md"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "assemble_mixed_512x512x256.md")
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -247,6 +248,8 @@ def run_ours(args):
                "steps": e2e_steps, "api": "tpfa_assemble_jacobian_host (pinned host buffers)"}
         del ph, Rh, vh, dh
 
+    jvp = None if args.skip_jvp else measure_jvp(g, prob, dev, stream, peak)
+
     # the plain FP64 path on the same grid, for the mixed-vs-FP64 line
     fp64 = None
     if not args.skip_fp64:
@@ -307,6 +310,7 @@ def run_ours(args):
         "fp64": fp64,
         "ensemble": ensemble,
         "adjoint": adjoint,
+        "jvp": jvp,
     }
     if rank == 0 and world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
@@ -383,6 +387,40 @@ def measure_ensemble(dev, stream, rank=0, world=1, reps=10):
             "launches_per_step": {"batched": 1, "sequential": len(mine)},
             "tiling": info, "scaling": "strong (fixed 64 models split across ranks)",
             "note": "one CUDA-graph launch of the persistent kernel vs one launch per model"}
+
+
+def measure_jvp(g, prob, dev, stream, peak, reps=10):
+    """Matrix-free J w (the Krylov operator) on the headline grid, mixed:
+    reads p, p^n, m^n, 5 owned T, depth and w; writes J w (56 B per cell)."""
+    import torch
+
+    from paper_2304_11274_gb300 import synth
+
+    w = torch.as_tensor(synth.cotangent(prob.n, synth.BASE_SEED + 40), device=dev)
+    Jw = torch.empty(prob.n, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        g.jvp(w, out=Jw)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.jvp(w, out=Jw)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    g.sync_status()
+    ms = a.elapsed_time(b) / reps
+    nbytes = prob.n * (4 + 4 + 8 + 5 * 4 + 4 + 8 + 8)
+    tiling = g.tiling()
+    khash = kernel_source_hash(JVP_SOURCES)
+    del w, Jw
+    return {"grid": [prob.nx, prob.ny, prob.nz], "value": prob.n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
+            "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": nbytes,
+                         "traffic": profiled_traffic(khash, "jvp_mixed_512x512x256.md"),
+                         "kernel_source_sha256_16": khash},
+            "kernel": "k_jvp_ymarch<DIAG,!CR,W=%d>" % tiling[1],
+            "tiling": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]},
+            "outputs": "J w (FP64)"}
 
 
 def measure_adjoint(dev, stream, reps=20):
@@ -477,6 +515,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--skip-ensemble", action="store_true", help="skip the 64-model batched ensemble line")
     ap.add_argument("--skip-adjoint", action="store_true", help="skip the adjoint (VJP) line")
+    ap.add_argument("--skip-jvp", action="store_true", help="skip the matrix-free J w line")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
                     help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")
     args = ap.parse_args()

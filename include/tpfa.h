@@ -171,6 +171,28 @@ int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream);
 int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_dev, void* stream);
 
 /*
+ * Matrix-free Jacobian-vector product at the bound state (the operator a
+ * Krylov solver of the backward-Euler system Eq. vk needs, without storing J):
+ *   Jw[K] = sum_L dR_K/dp_L w_L
+ *         = (dA_K/dp_K + sum_{L in adj(K)} dF_KL/dp_K) w_K + sum_L dF_KL/dp_L w_L
+ * with the flux of Eq. flux-calc and the same upwind rule (tie -> L) as the
+ * assembled Jacobian, so Jw equals the product of tpfa_assemble_jacobian's
+ * matrix with w up to FP64 rounding.  w_dev, Jw_dev: N doubles (device,
+ * caller-owned, w read and Jw written asynchronously on `stream`).
+ * R_dev: N doubles or NULL; when given it receives R of Eq. vk with exactly
+ * the bits tpfa_assemble_residual writes.  Links in the path's precision,
+ * the w-weighted sums in FP64.  Device-side errors (non-finite output, an
+ * out-of-range checked access) are reported by tpfa_sync_status.
+ */
+int tpfa_jvp(tpfa_handle h, const double* w_dev, double* Jw_dev, double* R_dev, void* stream);
+
+/* As tpfa_jvp with an explicit kernel variant (TPFA_MIXED: the tiled march
+ * and the naive gather give identical bits; TPFA_FP64 has one kernel and
+ * ignores the choice). */
+int tpfa_jvp_kernel(tpfa_handle h, tpfa_kernel kern, const double* w_dev, double* Jw_dev, double* R_dev,
+                    void* stream);
+
+/*
  * The static Jacobian pattern: row_ptr (N+1 int64) and col_idx (nnz int32),
  * columns ascending in each row.  Built on the first call (library-owned,
  * read-only, freed by destroy); synchronises `stream` on that first call.

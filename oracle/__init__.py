@@ -12,6 +12,8 @@ arrays through ctypes.  The functions follow the paper's notation:
 * ``assemble``  -- R of Eq. vk and J = dR/dp, cell loop then neighbour loop as
   in Algorithm 1
 * ``vjp``       -- v^T dR/dp and v^T dR/d(ln k)
+* ``jvp``       -- J w, the assembled Jacobian of Eq. vk times a vector (the
+  plain definition: a CSR matrix-vector product over ``assemble``'s J)
 * ``link_trans`` -- the transmissibility of one link
 """
 from __future__ import annotations
@@ -161,6 +163,18 @@ def vjp(nx, ny, nz, phys, perm, poro, depth, p, pn, v):
     if rc != 0:
         raise ValueError("oracle vjp failed")
     return g_p, g_lnk
+
+
+def jvp(nx, ny, nz, phys, perm, poro, depth, p, pn, w, pat=None):
+    """(J w, R): row K of J, in its CSR order, dotted with w (Eq. vk's
+    Jacobian applied to a direction), and the residual of the same state."""
+    out = assemble(nx, ny, nz, phys, perm, poro, depth, p, pn, pat=pat)
+    w = _f64(w).reshape(-1)
+    row_ptr, col_idx, J = out["row_ptr"], out["col_idx"], out["J"]
+    # every row holds its diagonal, so no row is empty and reduceat sums
+    # exactly the entries of each row
+    Jw = np.add.reduceat(J * w[col_idx], row_ptr[:-1])
+    return Jw, out["R"]
 
 
 def link_trans(phys, kK, kL, di, dj, dk):

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("tpfa_assemble_jacobian_host", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("tpfa_set_permeability", _I, [_VP, _VP, _VP]),
     ("tpfa_vjp", _I, [_VP, _VP, _VP, _VP, _VP]),
+    ("tpfa_jvp", _I, [_VP, _VP, _VP, _VP, _VP]),
+    ("tpfa_jvp_kernel", _I, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     ("tpfa_get_pattern", _I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_LL), _VP]),
     ("tpfa_copy_pattern", _I, [_VP, _VP, _VP, _VP]),
     ("tpfa_nnz", _LL, [_I, _I, _I, _I]),

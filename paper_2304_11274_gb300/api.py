@@ -160,6 +160,19 @@ class Grid:
         self._v = v
         return g_p, g_lnk
 
+    def jvp(self, w, want_residual=False, out=None, kernel="auto", stream=None):
+        """J w at the bound state without storing J (FP64); with
+        ``want_residual`` also R of the same pass.  Returns (Jw, R or None)."""
+        w = _dev_f64(w, self.device)
+        if w.numel() != self.n:
+            raise ValueError(f"expected {self.n} values, got {w.numel()}")
+        Jw = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
+        R = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_residual else None
+        check(self.lib.tpfa_jvp_kernel(self.handle, _capi.KERNELS[kernel], _ptr(w), _ptr(Jw), _ptr(R),
+                                       _stream(stream)))
+        self._w = w
+        return Jw, R
+
     def pattern(self, stream=None):
         """(row_ptr int64[N+1], col_idx int32[nnz]) as device tensors."""
         rp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)

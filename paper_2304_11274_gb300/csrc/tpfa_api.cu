@@ -394,6 +394,35 @@ int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_
     return TPFA_OK;
 }
 
+int tpfa_jvp_kernel(tpfa_handle h, tpfa_kernel kern, const double* w_dev, double* Jw_dev, double* R_dev,
+                    void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!w_dev || !Jw_dev) return fail(TPFA_ERR_INVALID_ARG, "w and Jw must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    AsmKernel k;
+    switch (kern) {
+        case TPFA_KERNEL_AUTO:
+        case TPFA_KERNEL_TILED: k = AsmKernel::YMarch; break;
+        case TPFA_KERNEL_NAIVE: k = AsmKernel::Naive; break;
+        default: return fail(TPFA_ERR_INVALID_ARG, "bad kernel variant %d", (int)kern);
+    }
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (h->prec == TPFA_MIXED)
+        e = launch_jvp_mixed(k, h->geom, h->qf, h->crk, fields_of<float>(h), w_dev, Jw_dev, R_dev, h->status, h->JY,
+                             h->W, st);
+    else
+        e = launch_jvp_fp64(h->geom, h->qd, h->crk, fields_of<double>(h), w_dev, Jw_dev, R_dev, h->status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "jvp launch");
+    return TPFA_OK;
+}
+
+int tpfa_jvp(tpfa_handle h, const double* w_dev, double* Jw_dev, double* R_dev, void* stream) {
+    return tpfa_jvp_kernel(h, TPFA_KERNEL_AUTO, w_dev, Jw_dev, R_dev, stream);
+}
+
 int tpfa_get_pattern(tpfa_handle h, const long long** row_ptr_dev, const int** col_idx_dev, long long* nnz,
                      void* stream) {
     int rc = check_handle(h);

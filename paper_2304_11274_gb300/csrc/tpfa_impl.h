@@ -48,6 +48,13 @@ cudaError_t launch_vjp_mixed(const GridGeom& g, const PhysF& q, bool crk, const 
 cudaError_t launch_vjp_fp64(const GridGeom& g, const PhysD& q, bool crk, const AsmFields<double>& f,
                             const double* kperm, const double* v, double* g_p, double* g_lnk,
                             unsigned int* status, cudaStream_t st);
+// Matrix-free J w (tpfa_jvp.cu); R may be null.  The mixed path runs the
+// y-march (JY rows per march, W warps per block) or the naive gather.
+cudaError_t launch_jvp_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
+                             const double* w, double* Jw, double* R, unsigned int* status, int JY, int W,
+                             cudaStream_t st);
+cudaError_t launch_jvp_fp64(const GridGeom& g, const PhysD& q, bool crk, const AsmFields<double>& f, const double* w,
+                            double* Jw, double* R, unsigned int* status, cudaStream_t st);
 cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st);
 cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st);
 

@@ -32,6 +32,10 @@
 // Every value goes through the same link()/accumulation() arithmetic and the
 // same summation order as assemble_row(), so this kernel and the naive one
 // produce identical bits.
+//
+// The same march also drives the matrix-free Jacobian-vector product of the
+// mixed path (JV = true, tpfa_jvp.cu): w joins the prefetched row inputs and
+// each row emits (J w)_K instead of a CSR row.
 #pragma once
 
 #include <type_traits>
@@ -82,8 +86,15 @@ __device__ __forceinline__ LinkOut<Real> link_t(const Phys& q, Real T, const Cel
     return r;
 }
 
-template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
+// w of one row for the Jacobian-vector product (FP32): the lane's cell and
+// its x-neighbours.
+struct YW {
+    float c, m, p;
+};
+
+template <typename Real, bool DIAG, bool CRK, bool JAC, int W, bool JV = false>
 struct YMarch {
+    static_assert(!JV || (sizeof(Real) == 4 && !JAC), "the J w march is the mixed path's, without CSR values");
     using Phys = typename PhysOf<Real>::type;
     static constexpr int VEC = 16 / (int)sizeof(Real);  // elements per 16-byte store
 
@@ -129,6 +140,12 @@ struct YMarch {
            F_HT1, F_HT2, NF };
     Real* ring;      // RING * NF * 32 values
     double* ringm;   // RING * 32 values of m^n
+    // J w mode: RING * NW * 32 values of w (own, halo, z-1, z+1), the
+    // direction w and the output
+    static constexpr int NW = 4;
+    double* ringw = nullptr;
+    const double* wv = nullptr;
+    double* Jw = nullptr;
 
     __device__ __forceinline__ void cp4(Real* dst, const Real* src, bool valid) const {
         const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -175,6 +192,13 @@ struct YMarch {
             cp4(R + F_HT2 * 32, h2l ? f.Tpp + (c - nx - 1) : f.Tmp + (h2r ? c - nx + 1 : c), h2l || h2r);
         }
         cp8(ringm + sl * 32 + lane, f.mn + c, a);
+        if constexpr (JV) {
+            double* Wr = ringw + sl * (NW * 32) + lane;
+            cp8(Wr, wv + c, a);
+            cp8(Wr + 32, wv + ch, rv && hact);
+            cp8(Wr + 64, wv + (zm ? c - nxy : c), a && zm);
+            cp8(Wr + 96, wv + (zp ? c + nxy : c), a && zp);
+        }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     // Wait until every requested row but the most recent one has arrived
@@ -207,6 +231,20 @@ struct YMarch {
         return make_row(R[F_P * 32], R[F_Z * 32], R[F_HP * 32], R[F_HZ * 32]);
     }
 
+    // w of the row in ring slot sl, narrowed to FP32 on the integer pipe
+    // (truncation, below one float ulp), x-neighbours by shuffles.
+    __device__ __forceinline__ YW w_row(int sl) const {
+        const double* Wr = ringw + sl * (NW * 32) + lane;
+        YW r;
+        r.c = narrow_rz(Wr[0]);
+        const float h = narrow_rz(Wr[32]);
+        r.m = vshfl_up(r.c);
+        r.p = vshfl_down(r.c);
+        if (lane == 0) r.m = h;
+        if (lane == 31) r.p = h;
+        return r;
+    }
+
     __device__ __forceinline__ YRow<Real> make_row(Real po, Real zo, Real ph, Real zh) const {
         YRow<Real> R;
         R.c = make_cell(q, po, zo);
@@ -237,15 +275,12 @@ struct YMarch {
         return U;
     }
 
-    // Assemble row j.  P, C, N: rows j-1, j, j+1.  Uprev: links from row j-1
-    // into row j.  buf: this step's staging buffer.  Returns the links from
-    // row j into row j+1.
-    template <bool FULL>
-    __device__ __forceinline__ YUp<Real> row(int j, const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
-                                             const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev, Real Tpp_prev,
-                                             Real Tmp_prev, Real* buf) const {
-        const int ey = FULL ? 2 : axis_links(j, ny);
-        const unsigned mask = FULL ? (DIAG ? 0x7ffu : 0x575u) : slot_mask(g, i, j, k);
+    // The ten links of row j (slot order), and the links from row j into
+    // row j+1 for the next step.
+    __device__ __forceinline__ void eval_links(const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
+                                               const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev,
+                                               Real Tpp_prev, Real Tmp_prev, LinkOut<Real> (&S)[NSLOT],
+                                               YUp<Real>& U) const {
         Real Tx_m = vshfl_up(D.Tx);
         if (lane == 0) Tx_m = D.hT1;
         const CellVal<Real> zmc = make_cell(q, D.p_zm, D.z_zm);
@@ -253,7 +288,6 @@ struct YMarch {
 
         // slot order: 0 (0,0,-1) 1 (-1,-1) 2 (0,-1) 3 (+1,-1) 4 (-1,0) 5 self
         //             6 (+1,0) 7 (-1,+1) 8 (0,+1) 9 (+1,+1) 10 (0,0,+1)
-        LinkOut<Real> S[NSLOT];
         LinkOut<Real> E;  // lane 0: its (-1,-1) link; lane 31: its (+1,-1) link
         if constexpr (sizeof(Real) == 4) {
             // eight links as four FP32x2 pairs
@@ -285,7 +319,6 @@ struct YMarch {
                 E = link(q, D.hT2, C.c, lane == 0 ? P.m : P.p);
             }
         }
-        YUp<Real> U;
         U.y = S[8];
         U.xy = S[9];
         U.mxy = S[7];
@@ -313,6 +346,20 @@ struct YMarch {
                 S[3] = link(q, Tr, C.c, P.p);
             }
         }
+    }
+
+    // Assemble row j.  P, C, N: rows j-1, j, j+1.  Uprev: links from row j-1
+    // into row j.  buf: this step's staging buffer.  Returns the links from
+    // row j into row j+1.
+    template <bool FULL>
+    __device__ __forceinline__ YUp<Real> row(int j, const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
+                                             const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev, Real Tpp_prev,
+                                             Real Tmp_prev, Real* buf) const {
+        const int ey = FULL ? 2 : axis_links(j, ny);
+        const unsigned mask = FULL ? (DIAG ? 0x7ffu : 0x575u) : slot_mask(g, i, j, k);
+        LinkOut<Real> S[NSLOT];
+        YUp<Real> U;
+        eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
 
         // offsets of this row's CSR segment and of this lane's row in it
         const int per = 1 + ey + ez, perx = 1 + g.diag * ey;
@@ -333,6 +380,43 @@ struct YMarch {
             const int iend = min(i0 + 32, nx);
             const int seg_len = (iend - i0) * per + (int)(axis_links_before(iend, nx) - Sx0) * perx;
             write_segment(buf, seg, aoff, seg_len);
+        }
+        return U;
+    }
+
+    // J w (and R when o.R is set) of row j: wP, wC, wN hold w of rows j-1,
+    // j, j+1; wzm, wzp the vertical neighbours'.  Per link the term
+    // dF/dp_K w_K + dF/dp_L w_L is one FP32 fma; the terms and the residual's
+    // fluxes share one FP32x2 Kahan sum in slot order, then dA/dp w_K.
+    template <bool FULL>
+    __device__ __forceinline__ YUp<Real> row_jvp(int j, const YRow<Real>& P, const YRow<Real>& C,
+                                                 const YRow<Real>& N, const YIn<Real>& D, const YUp<Real>& Uprev,
+                                                 Real Ty_prev, Real Tpp_prev, Real Tmp_prev, const YW& wP,
+                                                 const YW& wC, const YW& wN, float wzm, float wzp) const {
+        const unsigned mask = FULL ? (DIAG ? 0x7ffu : 0x575u) : slot_mask(g, i, j, k);
+        LinkOut<Real> S[NSLOT];
+        YUp<Real> U;
+        eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        const float ws[NSLOT] = {wzm, wP.m, wP.c, wP.p, wC.m, 0.f, wC.p, wN.m, wN.c, wN.p, wzp};
+        Kahan2 ks;
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+            if (s == SLOT_SELF) continue;
+            if (mask & (1u << s)) ks.add(f2(S[s].F, __fmaf_rn(S[s].Da, wC.c, __fmul_rn(S[s].Db, ws[s]))));
+        }
+        const AccF acc = accumulation<CRK>(q, C.c.p, D.pn, D.mn, C.c.rho, D.phi0);
+        Kahan32 js{ks.s.y, ks.c.y};
+        js.add(__fmul_rn(acc.dA, wC.c));
+        const double jw = __dadd_rn(widen(js.s), -widen(js.c));
+        if (act) {
+            const int c = kb + nx * j + i;
+            Jw[c] = jw;
+            double r = 0.0;
+            if (o.R) {
+                r = __dadd_rn(__dadd_rn(acc.A, widen(ks.s.x)), -widen(ks.c.x));
+                o.R[c] = r;
+            }
+            if (nonfinite(jw) || nonfinite(r)) atomicOr(o.status, STATUS_NONFINITE);
         }
         return U;
     }

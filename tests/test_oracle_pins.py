@@ -427,6 +427,45 @@ def test_vjp_pressure_matches_central_differences():
         assert fd == pytest.approx(float(g_p @ d), rel=1e-6)
 
 
+def test_jvp_matches_directional_central_differences():
+    """J w against (R(p + h w) - R(p - h w)) / 2h along random directions:
+    pins the CSR product of the oracle's J w to the residual itself."""
+    pr = _fd_problem()
+    args = (pr.nx, pr.ny, pr.nz, pr.phys, pr.perm, pr.poro, pr.depth)
+    rng = np.random.default_rng(16)
+    for _ in range(4):
+        w = rng.standard_normal(pr.n)
+        Jw, R = oracle.jvp(*args, pr.p, pr.pn, w)
+        assert np.array_equal(R, oracle.assemble(*args, pr.p, pr.pn)["R"])
+        h = 10.0  # Pa, as in the VJP differences
+        fd = (oracle.assemble(*args, pr.p + h * w, pr.pn)["R"] - oracle.assemble(*args, pr.p - h * w, pr.pn)["R"]) / (2 * h)
+        assert np.abs(fd - Jw).max() <= 1e-6 * np.abs(Jw).max()
+
+
+def test_jvp_dot_product_identity_with_adjoint():
+    """v^T (J w) = (J^T v)^T w with J w from the assembled CSR and J^T v from
+    the separate scatter-form adjoint."""
+    pr = _fd_problem()
+    args = (pr.nx, pr.ny, pr.nz, pr.phys, pr.perm, pr.poro, pr.depth, pr.p, pr.pn)
+    rng = np.random.default_rng(20)
+    for _ in range(3):
+        v, w = rng.standard_normal(pr.n), rng.standard_normal(pr.n)
+        Jw, _ = oracle.jvp(*args, w)
+        g_p, _ = oracle.vjp(*args, v)
+        assert float(v @ Jw) == pytest.approx(float(g_p @ w), rel=1e-11)
+
+
+def test_jvp_of_constant_direction_is_accumulation_only_when_incompressible():
+    """c_f = c_r = 0: rho is constant, the flux Jacobian is a weighted graph
+    Laplacian whose rows sum to zero, so J 1 = dA/dp = 0 as well (the
+    accumulation term is constant in p): J 1 vanishes to rounding."""
+    pr = synth.make_problem(4, 3, 3, seed=5, connectivity=10, c_f=0.0, c_r=0.0)
+    args = (pr.nx, pr.ny, pr.nz, pr.phys, pr.perm, pr.poro, pr.depth, pr.p, pr.pn)
+    Jw, _ = oracle.jvp(*args, np.ones(pr.n))
+    J = oracle.assemble(*args)["J"]
+    assert np.abs(Jw).max() <= 1e-13 * np.abs(J).max()
+
+
 def test_upwind_tie_takes_the_neighbour():
     """Section 3's upwind rule picks rho_K only when dPhi_KL > 0 and the
     neighbour's density otherwise, so at an exact tie each row uses the OTHER
