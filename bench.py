@@ -281,6 +281,7 @@ def run_ours(args):
 
     ensemble = None if args.skip_ensemble else measure_ensemble(dev, stream, rank, world)
     adjoint = None if (args.skip_adjoint or world > 1) else measure_adjoint(dev, stream)
+    newton = None if (args.skip_newton or world > 1) else measure_newton(dev, stream)
 
     line = {
         "metric": METRIC,
@@ -311,6 +312,7 @@ def run_ours(args):
         "ensemble": ensemble,
         "adjoint": adjoint,
         "jvp": jvp,
+        "newton": newton,
     }
     if rank == 0 and world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
@@ -423,6 +425,47 @@ def measure_jvp(g, prob, dev, stream, peak, reps=10):
             "outputs": "J w (FP64)"}
 
 
+def measure_newton(dev, stream, reps=3):
+    """One Newton step of Eq. vk (assemble, Jacobi-BiCGStab to rtol 1e-8,
+    update) on 128^3, 10 links, mixed, from the synthetic state; each timed
+    step restarts from the same p."""
+    import torch
+
+    from paper_2304_11274_gb300 import synth
+    from paper_2304_11274_gb300.api import Grid
+
+    prob = synth.config_problem(4)
+    g = Grid(prob.nx, prob.ny, prob.nz, prob.phys, "mixed", prob.perm, prob.poro, prob.depth, device=dev)
+    p0 = torch.as_tensor(prob.p.astype(np.float32), device=dev)
+    g.set_state(p0, torch.as_tensor(prob.pn.astype(np.float32), device=dev))
+    p = p0.clone()
+    g.newton_step(p, rtol=1e-8, max_iters=5000)  # warm-up (allocates the workspace)
+    times, iters = [], []
+    for _ in range(reps):
+        p.copy_(p0)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, _, _ = g.newton_step(p, rtol=1e-8, max_iters=5000)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(a.elapsed_time(b))
+        iters.append(st["iterations"])
+    g.sync_status()
+    ms = statistics.median(times)
+    it = statistics.median(iters)
+    per_iter_bytes = 8 * g.nnz + 216 * prob.n  # two stencil SpMVs (FP32 values) + the FP64 vector updates
+    ms_iter = ms / max(it, 1)
+    g.close()
+    peak, _ = measured_peaks()
+    return {"grid": [prob.nx, prob.ny, prob.nz], "unit": "ms per Newton step", "ms": ms,
+            "krylov_iterations": it, "ms_per_iteration": ms_iter, "rtol": 1e-8,
+            "roofline_per_iteration": {"bound": "hbm", "algorithmic_bytes": per_iter_bytes,
+                                       "achieved": per_iter_bytes / (ms_iter * 1e-3) / 1e9, "peak": peak,
+                                       "unit": "GB/s", "frac": per_iter_bytes / (ms_iter * 1e-3) / 1e9 / peak},
+            "note": "includes one assembly and the update; 8 launches per BiCGStab iteration, host poll every 8"}
+
+
 def measure_adjoint(dev, stream, reps=20):
     """Adjoint (v^T dR/dp and v^T dR/d ln k) on 128^3, 10 links, mixed."""
     import torch
@@ -516,6 +559,7 @@ def main():
     ap.add_argument("--skip-ensemble", action="store_true", help="skip the 64-model batched ensemble line")
     ap.add_argument("--skip-adjoint", action="store_true", help="skip the adjoint (VJP) line")
     ap.add_argument("--skip-jvp", action="store_true", help="skip the matrix-free J w line")
+    ap.add_argument("--skip-newton", action="store_true", help="skip the Newton-step line")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
                     help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")
     args = ap.parse_args()

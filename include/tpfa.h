@@ -54,6 +54,7 @@ extern "C" {
 #define TPFA_ERR_NO_STATE (-6)    /* assemble called before tpfa_set_state */
 #define TPFA_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out */
 #define TPFA_ERR_DEVICE_CHECK (-8) /* a device-side bounds check failed (nothing was accessed) */
+#define TPFA_ERR_NO_CONVERGENCE (-9) /* the Krylov solve stopped before its tolerance (breakdown or iteration limit) */
 
 typedef struct tpfa_grid* tpfa_handle; /* opaque, library-owned */
 
@@ -250,6 +251,58 @@ int tpfa_get_tiling(tpfa_handle h, int* rows_per_march, int* warps_per_block);
  * temporary outputs on `stream` and synchronises it.
  */
 int tpfa_autotune(tpfa_handle h, const char* cache_path, void* stream);
+
+/* ---------------------------------------------------------------- Newton step */
+
+/*
+ * One Newton iteration on the backward-Euler system Eq. vk (R(p^{n+1}) = 0):
+ *   assemble R(p^k) and J = dR/dp at p^k (the fused kernel of
+ *   tpfa_assemble_jacobian), solve J delta = -R with BiCGStab right-
+ *   preconditioned by the Jacobi (diagonal) preconditioner, p^{k+1} = p^k + delta.
+ * The paper names the implicit system and a Krylov solve of it as the use of
+ * the flux operator but fixes neither the nonlinear nor the linear method;
+ * these are the standard choices.  Vectors, dot products and the update are
+ * FP64; the matrix is the path's assembled Jacobian (FP32 off-diagonals with
+ * FP64 diagonal on TPFA_MIXED).  The matrix-vector product walks the
+ * structured stencil (columns follow from the closed-form pattern), and the
+ * solver's scalars live on the device: the host reads them every
+ * `check_every` iterations.
+ */
+typedef struct {
+    int max_iters;    /* BiCGStab iteration limit (<= 0: 1000) */
+    double rtol;      /* stop when ||b - J x||_2 <= rtol ||b||_2 (<= 0: 1e-8) */
+    int check_every;  /* iterations between host convergence checks (<= 0: 8) */
+} tpfa_krylov_opts;
+
+typedef struct {
+    int iterations;       /* BiCGStab iterations taken */
+    int converged;        /* 1 if the tolerance was met */
+    int breakdown;        /* 1 if a BiCGStab denominator vanished */
+    double b_norm;        /* ||b||_2 (for a Newton step: ||R(p^k)||_2) */
+    double rel_residual;  /* ||b - J x||_2 / ||b||_2 of the recursively updated residual */
+} tpfa_krylov_stats;
+
+/*
+ * Solve J x = b, J the Jacobian at the bound state (assembled into
+ * library-owned workspace by this call), x0 = 0.  b_dev, x_dev: N doubles
+ * (device, caller-owned).  opts may be NULL (defaults); stats may be NULL.
+ * Synchronous on `stream`.  Returns TPFA_ERR_NO_CONVERGENCE when the
+ * tolerance was not met (x_dev then holds the last iterate).  The first
+ * call allocates the workspace: nnz values, 10 FP64 vectors of N.
+ */
+int tpfa_linear_solve(tpfa_handle h, const double* b_dev, double* x_dev, const tpfa_krylov_opts* opts,
+                      tpfa_krylov_stats* stats, void* stream);
+
+/*
+ * One Newton step in place: binds p_dev as the pressure (as
+ * tpfa_set_pressure; N values of the field type), solves J delta = -R(p) as
+ * tpfa_linear_solve does and writes p + delta back to p_dev (rounded to the
+ * field type).  R_dev: N doubles or NULL, receives R(p) before the update.
+ * delta_dev: N doubles or NULL, receives delta.  On
+ * TPFA_ERR_NO_CONVERGENCE p_dev is left unchanged.  Synchronous on `stream`.
+ */
+int tpfa_newton_step(tpfa_handle h, void* p_dev, const tpfa_krylov_opts* opts, tpfa_krylov_stats* stats,
+                     double* R_dev, double* delta_dev, void* stream);
 
 /* ---------------------------------------------------------------- ensembles */
 

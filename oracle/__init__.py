@@ -14,6 +14,8 @@ arrays through ctypes.  The functions follow the paper's notation:
 * ``vjp``       -- v^T dR/dp and v^T dR/d(ln k)
 * ``jvp``       -- J w, the assembled Jacobian of Eq. vk times a vector (the
   plain definition: a CSR matrix-vector product over ``assemble``'s J)
+* ``newton_step`` -- one Newton iteration on Eq. vk, J delta = -R solved
+  directly (sparse LU), p + delta
 * ``link_trans`` -- the transmissibility of one link
 """
 from __future__ import annotations
@@ -175,6 +177,23 @@ def jvp(nx, ny, nz, phys, perm, poro, depth, p, pn, w, pat=None):
     # exactly the entries of each row
     Jw = np.add.reduceat(J * w[col_idx], row_ptr[:-1])
     return Jw, out["R"]
+
+
+def jacobian_csr(out, n):
+    """assemble()'s J as a scipy CSR matrix."""
+    import scipy.sparse as sp
+    return sp.csr_matrix((out["J"], out["col_idx"], out["row_ptr"]), shape=(n, n))
+
+
+def newton_step(nx, ny, nz, phys, perm, poro, depth, p, pn):
+    """(p + delta, delta, R): Newton's method on R(p) = 0 (Eq. vk, backward
+    Euler), the linear system J delta = -R solved by sparse LU."""
+    from scipy.sparse.linalg import spsolve
+    p = _f64(p).reshape(-1)
+    out = assemble(nx, ny, nz, phys, perm, poro, depth, p, pn)
+    J = jacobian_csr(out, nx * ny * nz)
+    delta = np.atleast_1d(spsolve(J.tocsc(), -out["R"]))
+    return p + delta, delta, out["R"]
 
 
 def link_trans(phys, kK, kL, di, dj, dk):

@@ -21,6 +21,7 @@ ERRORS = {
     -6: "TPFA_ERR_NO_STATE",
     -7: "TPFA_ERR_TIMEOUT",
     -8: "TPFA_ERR_DEVICE_CHECK",
+    -9: "TPFA_ERR_NO_CONVERGENCE",
 }
 TPFA_FP64, TPFA_MIXED = 0, 1
 KERNELS = {"auto": 0, "naive": 1, "tiled": 2}
@@ -49,6 +50,20 @@ class TPFAParams(ctypes.Structure):
     ]
 
 
+class TPFAKrylovOpts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("check_every", ctypes.c_int)]
+
+
+class TPFAKrylovStats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("breakdown", ctypes.c_int),
+        ("b_norm", ctypes.c_double),
+        ("rel_residual", ctypes.c_double),
+    ]
+
+
 # (name, restype, argtypes) of every exported symbol.
 _VP, _I, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
 SIGNATURES = [
@@ -63,6 +78,9 @@ SIGNATURES = [
     ("tpfa_vjp", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_jvp", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_jvp_kernel", _I, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    ("tpfa_linear_solve", _I, [_VP, _VP, _VP, ctypes.POINTER(TPFAKrylovOpts), ctypes.POINTER(TPFAKrylovStats), _VP]),
+    ("tpfa_newton_step", _I, [_VP, _VP, ctypes.POINTER(TPFAKrylovOpts), ctypes.POINTER(TPFAKrylovStats), _VP, _VP,
+                              _VP]),
     ("tpfa_get_pattern", _I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_LL), _VP]),
     ("tpfa_copy_pattern", _I, [_VP, _VP, _VP, _VP]),
     ("tpfa_nnz", _LL, [_I, _I, _I, _I]),

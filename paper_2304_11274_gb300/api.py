@@ -55,6 +55,8 @@ class Grid:
         self.phys = dict(phys)
         self.precision = precision
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.dtype = torch.float32 if precision == "mixed" else torch.float64
         prm = params_struct(self.phys)
         with torch.cuda.device(self.device):
@@ -172,6 +174,49 @@ class Grid:
                                        _stream(stream)))
         self._w = w
         return Jw, R
+
+    @staticmethod
+    def _krylov(rtol, max_iters, check_every):
+        return _capi.TPFAKrylovOpts(int(max_iters), float(rtol), int(check_every))
+
+    @staticmethod
+    def _stats(st):
+        return {k: getattr(st, k) for k, _ in _capi.TPFAKrylovStats._fields_}
+
+    def linear_solve(self, b, rtol=1e-8, max_iters=1000, check_every=8, out=None, stream=None):
+        """x with J x = b (J at the bound state; Jacobi-preconditioned
+        BiCGStab, FP64 vectors).  Returns (x, stats); raises TPFAError
+        (TPFA_ERR_NO_CONVERGENCE) if the tolerance is not met."""
+        b = _dev_f64(b, self.device)
+        if b.numel() != self.n:
+            raise ValueError(f"expected {self.n} values, got {b.numel()}")
+        x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
+        st = _capi.TPFAKrylovStats()
+        opts = self._krylov(rtol, max_iters, check_every)
+        rc = self.lib.tpfa_linear_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(st),
+                                        _stream(stream))
+        self.last_stats = self._stats(st)
+        check(rc)
+        return x, self.last_stats
+
+    def newton_step(self, p, rtol=1e-8, max_iters=1000, check_every=8, want_residual=False, want_delta=False,
+                    stream=None):
+        """One Newton step of Eq. vk in place on p (a device tensor of the
+        field dtype, bound as the pressure).  Returns (stats, R(p) or None,
+        delta or None)."""
+        if not isinstance(p, torch.Tensor) or p.device != self.device or p.dtype != self.dtype \
+                or not p.is_contiguous() or p.numel() != self.n:
+            raise ValueError("p must be a contiguous device tensor of the field dtype with N values")
+        R = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_residual else None
+        d = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_delta else None
+        st = _capi.TPFAKrylovStats()
+        opts = self._krylov(rtol, max_iters, check_every)
+        self._p = p
+        rc = self.lib.tpfa_newton_step(self.handle, _ptr(p), ctypes.byref(opts), ctypes.byref(st), _ptr(R),
+                                       _ptr(d), _stream(stream))
+        self.last_stats = self._stats(st)
+        check(rc)
+        return self.last_stats, R, d
 
     def pattern(self, stream=None):
         """(row_ptr int64[N+1], col_idx int32[nnz]) as device tensors."""

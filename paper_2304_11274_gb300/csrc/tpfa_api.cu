@@ -106,8 +106,24 @@ struct tpfa_grid {
     double* h_R = nullptr;
     void* h_vals = nullptr;
     double* h_diag = nullptr;
+    // Newton / Krylov workspace, allocated on first use
+    void* kv_vals = nullptr;
+    double* kv_diag = nullptr;
+    double* kv_R = nullptr;
+    double* kv_vec[10] = {};  // x, r, r^, p, p^, v, s, s^, t, M^-1
+    double* kv_part = nullptr;
+    KrylovScalars* kv_S = nullptr;
+    KrylovScalars* kv_S_host = nullptr;  // pinned
 
     void release() {
+        dev_free(kv_vals);
+        dev_free(kv_diag);
+        dev_free(kv_R);
+        for (auto& v : kv_vec) dev_free(v), v = nullptr;
+        dev_free(kv_part);
+        dev_free(kv_S);
+        if (kv_S_host) cudaFreeHost(kv_S_host);
+        kv_vals = nullptr, kv_diag = nullptr, kv_R = nullptr, kv_part = nullptr, kv_S = nullptr, kv_S_host = nullptr;
         for (auto& t : T) dev_free(t), t = nullptr;
         dev_free(z);
         dev_free(kperm);
@@ -176,6 +192,89 @@ int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, 
 
 int check_handle(tpfa_handle h) {
     if (!h) return fail(TPFA_ERR_INVALID_ARG, "handle is NULL");
+    return TPFA_OK;
+}
+
+// Newton / Krylov workspace: the assembled Jacobian, R, ten FP64 vectors,
+// the partial sums and the scalar record (device and pinned host copies).
+int krylov_workspace(tpfa_grid* h) {
+    if (h->kv_S_host) return TPFA_OK;
+    const size_t nb = sizeof(double) * (size_t)h->N;
+    bool ok = dev_alloc(&h->kv_vals, h->real_size * (size_t)h->nnz) == cudaSuccess;
+    if (ok && h->prec == TPFA_MIXED) ok = dev_alloc((void**)&h->kv_diag, nb) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&h->kv_R, nb) == cudaSuccess;
+    for (auto& v : h->kv_vec) ok = ok && dev_alloc((void**)&v, nb) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&h->kv_part, sizeof(double) * 2 * (size_t)krylov_partials(h->geom, h->N)) ==
+                   cudaSuccess;
+    ok = ok && dev_alloc((void**)&h->kv_S, sizeof(KrylovScalars)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&h->kv_S_host, sizeof(KrylovScalars)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        dev_free(h->kv_vals);
+        dev_free(h->kv_diag);
+        dev_free(h->kv_R);
+        for (auto& v : h->kv_vec) dev_free(v), v = nullptr;
+        dev_free(h->kv_part);
+        dev_free(h->kv_S);
+        if (h->kv_S_host) cudaFreeHost(h->kv_S_host);
+        h->kv_vals = nullptr, h->kv_diag = nullptr, h->kv_R = nullptr, h->kv_part = nullptr, h->kv_S = nullptr;
+        h->kv_S_host = nullptr;
+        return fail(TPFA_ERR_OOM, "device allocation failed for the Newton/Krylov workspace");
+    }
+    return TPFA_OK;
+}
+
+// Solve J x = sign * b with the Jacobian held in the workspace.
+int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tpfa_krylov_opts* opts,
+                 tpfa_krylov_stats* stats, cudaStream_t st) {
+    const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 1000;
+    const double rtol = (opts && opts->rtol > 0.0) ? opts->rtol : 1e-8;
+    const int every = (opts && opts->check_every > 0) ? opts->check_every : 8;
+    const bool mixed = h->prec == TPFA_MIXED;
+    KrylovWork w;
+    w.x = x;
+    w.r = h->kv_vec[1];
+    w.rh = h->kv_vec[2];
+    w.p = h->kv_vec[3];
+    w.ph = h->kv_vec[4];
+    w.v = h->kv_vec[5];
+    w.s = h->kv_vec[6];
+    w.sh = h->kv_vec[7];
+    w.t = h->kv_vec[8];
+    w.dinv = h->kv_vec[9];
+    w.part = h->kv_part;
+    w.S = h->kv_S;
+    KrylovScalars* Sh = h->kv_S_host;
+    *Sh = KrylovScalars{};
+    Sh->tol2 = rtol * rtol;
+    Sh->max_iters = max_iters;
+    cudaError_t e = cudaMemcpyAsync(w.S, Sh, sizeof(KrylovScalars), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = krylov_dinv(h->geom, mixed, h->kv_vals, h->kv_diag, w.dinv, st);
+    if (e == cudaSuccess) e = krylov_start(h->geom, h->N, b, sign, w, st);
+    if (e != cudaSuccess) return cuda_fail(e, "Krylov start");
+    // every kernel returns at entry once `done` is set, so batches of
+    // `every` iterations may overshoot the stopping point harmlessly; the
+    // device stops at max_iters, so this loop ends after at most
+    // max_iters / every + 1 polls
+    for (int it = 0; it <= max_iters + every; it += every) {
+        for (int q = 0; q < every && e == cudaSuccess; ++q)
+            e = krylov_iteration(h->geom, h->N, mixed, h->kv_vals, h->kv_diag, w, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Sh, w.S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "Krylov iteration");
+        if (Sh->done) break;
+    }
+    const bool converged = Sh->done && !Sh->breakdown && Sh->rr <= Sh->tol2 * Sh->bb;
+    if (stats) {
+        stats->iterations = Sh->iter;
+        stats->converged = converged ? 1 : 0;
+        stats->breakdown = Sh->breakdown;
+        stats->b_norm = sqrt(Sh->bb);
+        stats->rel_residual = Sh->bb > 0.0 ? sqrt(Sh->rr / Sh->bb) : 0.0;
+    }
+    if (!converged)
+        return fail(TPFA_ERR_NO_CONVERGENCE, "BiCGStab stopped after %d iterations at relative residual %.3e%s",
+                    Sh->iter, Sh->bb > 0.0 ? sqrt(Sh->rr / Sh->bb) : 0.0, Sh->breakdown ? " (breakdown)" : "");
     return TPFA_OK;
 }
 
@@ -421,6 +520,44 @@ int tpfa_jvp_kernel(tpfa_handle h, tpfa_kernel kern, const double* w_dev, double
 
 int tpfa_jvp(tpfa_handle h, const double* w_dev, double* Jw_dev, double* R_dev, void* stream) {
     return tpfa_jvp_kernel(h, TPFA_KERNEL_AUTO, w_dev, Jw_dev, R_dev, stream);
+}
+
+int tpfa_linear_solve(tpfa_handle h, const double* b_dev, double* x_dev, const tpfa_krylov_opts* opts,
+                      tpfa_krylov_stats* stats, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!b_dev || !x_dev) return fail(TPFA_ERR_INVALID_ARG, "b and x must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    DeviceGuard dg(h->device);
+    rc = krylov_workspace(h);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = launch(h, AsmKernel::YMarch, nullptr, h->kv_vals, h->prec == TPFA_MIXED ? h->kv_diag : nullptr, st);
+    if (rc) return rc;
+    return krylov_solve(h, b_dev, 1.0, x_dev, opts, stats, st);
+}
+
+int tpfa_newton_step(tpfa_handle h, void* p_dev, const tpfa_krylov_opts* opts, tpfa_krylov_stats* stats,
+                     double* R_dev, double* delta_dev, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!p_dev) return fail(TPFA_ERR_INVALID_ARG, "p must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    DeviceGuard dg(h->device);
+    rc = krylov_workspace(h);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    h->p = p_dev;
+    double* R = R_dev ? R_dev : h->kv_R;
+    double* x = delta_dev ? delta_dev : h->kv_vec[0];
+    rc = launch(h, AsmKernel::YMarch, R, h->kv_vals, h->prec == TPFA_MIXED ? h->kv_diag : nullptr, st);
+    if (rc) return rc;
+    rc = krylov_solve(h, R, -1.0, x, opts, stats, st);
+    if (rc) return rc;
+    cudaError_t e = krylov_add_delta(h->N, h->prec == TPFA_MIXED, p_dev, x, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "Newton update");
+    return TPFA_OK;
 }
 
 int tpfa_get_pattern(tpfa_handle h, const long long** row_ptr_dev, const int** col_idx_dev, long long* nnz,

@@ -58,6 +58,28 @@ cudaError_t launch_jvp_fp64(const GridGeom& g, const PhysD& q, bool crk, const A
 cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st);
 cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st);
 
+// Jacobi-preconditioned BiCGStab (tpfa_krylov.cu).  The scalars live on the
+// device; the host polls them.
+struct KrylovScalars {
+    double rho, alpha, omega, beta, rr, bb, tol2;
+    int done, breakdown, iter, max_iters;
+};
+struct KrylovWork {
+    double *x, *r, *rh, *p, *ph, *v, *s, *sh, *t, *dinv;
+    double* part;  // 2 * krylov_partials() per-block partial sums
+    KrylovScalars* S;
+};
+long long krylov_vec_blocks(long long n);
+long long krylov_partials(const GridGeom& g, long long n);
+cudaError_t krylov_dinv(const GridGeom& g, bool mixed, const void* vals, const double* diag64, double* dinv,
+                        cudaStream_t st);
+// x = 0, r = r^ = sign * b, scalars initialised (S->tol2, S->max_iters set by the caller)
+cudaError_t krylov_start(const GridGeom& g, long long n, const double* b, double sign, const KrylovWork& w,
+                         cudaStream_t st);
+cudaError_t krylov_iteration(const GridGeom& g, long long n, bool mixed, const void* vals, const double* diag64,
+                             const KrylovWork& w, cudaStream_t st);
+cudaError_t krylov_add_delta(long long n, bool mixed, void* p, const double* d, cudaStream_t st);
+
 // Sets the thread-local message of tpfa_last_error_string and returns code.
 int report_error(int code, const char* msg);
 

@@ -466,6 +466,35 @@ def test_jvp_of_constant_direction_is_accumulation_only_when_incompressible():
     assert np.abs(Jw).max() <= 1e-13 * np.abs(J).max()
 
 
+def test_newton_step_solves_linear_problem_exactly():
+    """c_f = 0 with c_r != 0: rho is constant and phi linear in p, so R is
+    affine in p (the upwind choice does not change rho_up) and one Newton
+    step lands on R = 0 up to rounding."""
+    pr = synth.make_problem(6, 5, 4, seed=31, connectivity=10, c_f=0.0, c_r=1e-8)
+    args = (pr.nx, pr.ny, pr.nz, pr.phys, pr.perm, pr.poro, pr.depth)
+    p1, delta, R0 = oracle.newton_step(*args, pr.p, pr.pn)
+    R1 = oracle.assemble(*args, p1, pr.pn)["R"]
+    assert np.abs(R0).max() > 0
+    assert np.abs(R1).max() <= 1e-9 * np.abs(R0).max()
+    assert np.abs(delta).max() > 1.0  # a real step, not a no-op
+
+
+def test_newton_converges_superlinearly():
+    """A strongly compressible fluid (c_f = 1e-7 /Pa, c_r = 1e-8 /Pa): the
+    residual ratio shrinks from step to step (quadratic convergence), where a
+    wrong Jacobian entry would leave it roughly constant."""
+    pr = synth.make_problem(6, 5, 4, seed=33, connectivity=10, c_f=1e-7, c_r=1e-8)
+    args = (pr.nx, pr.ny, pr.nz, pr.phys, pr.perm, pr.poro, pr.depth)
+    p = pr.p.copy()
+    norms = [np.abs(oracle.assemble(*args, p, pr.pn)["R"]).max()]
+    for _ in range(3):
+        p, _, _ = oracle.newton_step(*args, p, pr.pn)
+        norms.append(np.abs(oracle.assemble(*args, p, pr.pn)["R"]).max())
+    r = [norms[k + 1] / norms[k] for k in range(3)]
+    assert r[0] < 0.5
+    assert r[1] < 0.2 * r[0] or norms[2] <= 1e-12 * norms[0]
+
+
 def test_upwind_tie_takes_the_neighbour():
     """Section 3's upwind rule picks rho_K only when dPhi_KL > 0 and the
     neighbour's density otherwise, so at an exact tie each row uses the OTHER
