@@ -40,6 +40,7 @@ CONN = 10
 WORKLOAD = "tpfa_residual_jacobian_512x512x256_10pt_mixed"
 KERNEL_SOURCES = ["tpfa_assemble.cu", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
 JVP_SOURCES = ["tpfa_jvp.cu", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
+MESH_SOURCES = ["tpfa_mesh.cu", "tpfa_mesh.h", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
 
 
 def env_rank():
@@ -282,6 +283,7 @@ def run_ours(args):
     ensemble = None if args.skip_ensemble else measure_ensemble(dev, stream, rank, world)
     adjoint = None if (args.skip_adjoint or world > 1) else measure_adjoint(dev, stream)
     newton = None if (args.skip_newton or world > 1) else measure_newton(dev, stream)
+    mesh = None if (args.skip_mesh or world > 1) else measure_mesh(dev, stream)
 
     line = {
         "metric": METRIC,
@@ -313,6 +315,7 @@ def run_ours(args):
         "adjoint": adjoint,
         "jvp": jvp,
         "newton": newton,
+        "mesh": mesh,
     }
     if rank == 0 and world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
@@ -423,6 +426,47 @@ def measure_jvp(g, prob, dev, stream, peak, reps=10):
             "kernel": "k_jvp_ymarch<DIAG,!CR,W=%d>" % tiling[1],
             "tiling": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]},
             "outputs": "J w (FP64)"}
+
+
+def measure_mesh(dev, stream, reps=20):
+    """Residual + Jacobian on a faulted corner-point-like mesh given as a
+    connection list: 256 x 256 x 128 cells before 5 % pinch-outs, 10 links
+    per cell plus the fault's non-neighbour connections, mixed."""
+    import torch
+
+    from paper_2304_11274_gb300 import synth
+    from paper_2304_11274_gb300.api import Mesh
+
+    m = synth.make_mesh(256, 256, 128, seed=synth.BASE_SEED + 5, connectivity=10)
+    g = Mesh(m.n, m.ci, m.cj, m.T, m.V, m.poro, m.depth, m.phys, "mixed", device=dev)
+    g.set_state(m.p.astype(np.float32), m.pn.astype(np.float32))
+    R, vals, diag = g.empty_outputs()
+    for _ in range(3):
+        g.assemble(R, vals, diag)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.assemble(R, vals, diag)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    g.sync_status()
+    ms = a.elapsed_time(b) / reps
+    # per cell: row_ptr 8, p 4, p^n 4, m^n 8, depth 4 read, R 8 and diag64 8 written;
+    # per entry: col_idx 4 read and the value 4 written; per off-diagonal entry: T 4 read
+    nbytes = m.n * (8 + 4 + 4 + 8 + 4 + 8 + 8) + g.nnz * (4 + 4) + (g.nnz - m.n) * 4
+    peak, _ = measured_peaks()
+    khash = kernel_source_hash(MESH_SOURCES)
+    out = {"cells": m.n, "connections": m.nc, "nnz": g.nnz, "value": m.n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
+           "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": nbytes,
+                        "traffic": profiled_traffic(khash, "mesh_mixed_256x256x128_faulted.md"),
+                        "kernel_source_sha256_16": khash},
+           "kernel": "k_mesh_assemble<float,!CR,JAC>",
+           "workload": "faulted mesh 256x256x128, 10 links + fault NNCs, 5 % inactive, mixed"}
+    del R, vals, diag
+    g.close()
+    return out
 
 
 def measure_newton(dev, stream, reps=3):
@@ -560,6 +604,7 @@ def main():
     ap.add_argument("--skip-adjoint", action="store_true", help="skip the adjoint (VJP) line")
     ap.add_argument("--skip-jvp", action="store_true", help="skip the matrix-free J w line")
     ap.add_argument("--skip-newton", action="store_true", help="skip the Newton-step line")
+    ap.add_argument("--skip-mesh", action="store_true", help="skip the general-mesh line")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
                     help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")
     args = ap.parse_args()

@@ -304,6 +304,57 @@ int tpfa_linear_solve(tpfa_handle h, const double* b_dev, double* x_dev, const t
 int tpfa_newton_step(tpfa_handle h, void* p_dev, const tpfa_krylov_opts* opts, tpfa_krylov_stats* stats,
                      double* R_dev, double* delta_dev, void* stream);
 
+/* ---------------------------------------------------------------- general meshes */
+
+typedef struct tpfa_mesh_s* tpfa_mesh; /* opaque, library-owned */
+
+/*
+ * A general mesh given as a list of connections, the extension to arbitrary
+ * mesh topologies (corner-point grids with faults and non-neighbour
+ * connections, unstructured meshes) that Section 8 names as future work.
+ * adj(K) is every cell sharing a connection with K; the flux of connection
+ * (K, L) is Eq. flux-calc with Upsilon_KL given, the accumulation is Eq. vk's
+ * with the cell's own volume V_K, and upwinding, density and porosity are as
+ * on the structured grid (same arithmetic, same precision paths).
+ *   n_cells, n_conn     : cells (< 2^31) and connections (>= 0)
+ *   prm                 : rho_ref, p_ref, c_f, mu, g, dt, c_r are used;
+ *                         dx, dy, dz and connectivity are ignored
+ *   conn_i_dev, conn_j_dev : n_conn int32 cell indices each; i != j, both in
+ *                         [0, n_cells), no pair listed twice (in either order)
+ *   trans_dev           : n_conn Upsilon_KL (m^3, >= 0), FP64
+ *   volume_dev, poro_dev, depth_dev : n_cells FP64 (m^3, -, m positive down)
+ * All inputs are read during the call (copied, device, caller-owned).  The
+ * pattern (row K: K and its neighbours, columns ascending, int64 row_ptr and
+ * int32 col_idx) is built on the host and uploaded; the call synchronises
+ * `stream`.  Bad lists return TPFA_ERR_INVALID_ARG with the first offending
+ * connection in the message.
+ */
+int tpfa_create_mesh(tpfa_mesh* out, long long n_cells, long long n_conn, const tpfa_params* prm,
+                     tpfa_precision prec, const int* conn_i_dev, const int* conn_j_dev, const double* trans_dev,
+                     const double* volume_dev, const double* poro_dev, const double* depth_dev, void* stream);
+
+/* As tpfa_set_state / tpfa_set_pressure: n_cells values of the field type;
+ * m^n = (V_K/dt) phi(p^n) rho(p^n) is computed here. */
+int tpfa_mesh_set_state(tpfa_mesh m, const void* p_dev, const void* p_prev_dev, void* stream);
+int tpfa_mesh_set_pressure(tpfa_mesh m, const void* p_dev);
+
+/* Residual and Jacobian (as tpfa_assemble_jacobian, in the CSR order of the
+ * mesh's pattern); vals_dev NULL assembles the residual only. */
+int tpfa_mesh_assemble(tpfa_mesh m, double* R_dev, void* vals_dev, double* diag64_dev, void* stream);
+
+/* Copy the pattern into caller-owned device buffers (either may be NULL):
+ * row_ptr (n_cells + 1 int64), col_idx (nnz int32). */
+int tpfa_mesh_copy_pattern(tpfa_mesh m, long long* row_ptr_out_dev, int* col_idx_out_dev, void* stream);
+
+/* Sizes: cells, connections, Jacobian entries (n_cells + 2 n_conn), precision. */
+int tpfa_mesh_info(tpfa_mesh m, long long* n_cells, long long* n_conn, long long* nnz, int* precision);
+
+/* As tpfa_sync_status. */
+int tpfa_mesh_sync_status(tpfa_mesh m, void* stream);
+
+/* Free the mesh; NULL-safe.  Synchronises the device. */
+int tpfa_destroy_mesh(tpfa_mesh m);
+
 /* ---------------------------------------------------------------- ensembles */
 
 typedef struct tpfa_ensemble_s* tpfa_ensemble; /* opaque, library-owned */

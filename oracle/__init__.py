@@ -16,6 +16,9 @@ arrays through ctypes.  The functions follow the paper's notation:
   plain definition: a CSR matrix-vector product over ``assemble``'s J)
 * ``newton_step`` -- one Newton iteration on Eq. vk, J delta = -R solved
   directly (sparse LU), p + delta
+* ``mesh_pattern``, ``mesh_assemble`` -- the same residual and Jacobian on a
+  general mesh given as a list of connections (K, L, Upsilon_KL) with
+  per-cell volumes
 * ``link_trans`` -- the transmissibility of one link
 """
 from __future__ import annotations
@@ -75,6 +78,10 @@ def _load():
     lib.orc_vjp.restype = ctypes.c_int
     lib.orc_link_trans.argtypes = [P(OracleParams), ctypes.c_double, ctypes.c_double] + [ctypes.c_int] * 3
     lib.orc_link_trans.restype = ctypes.c_double
+    lib.orc_mesh_pattern.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ll, ll, ll, ll, ll]
+    lib.orc_mesh_pattern.restype = ctypes.c_longlong
+    lib.orc_mesh_assemble.argtypes = [ctypes.c_longlong, P(OracleParams)] + [d] * 6 + [ll, ll, ll, u8] + [d] * 5
+    lib.orc_mesh_assemble.restype = ctypes.c_int
     lib.orc_max_threads.argtypes = []
     lib.orc_max_threads.restype = ctypes.c_int
     _lib = lib
@@ -194,6 +201,60 @@ def newton_step(nx, ny, nz, phys, perm, poro, depth, p, pn):
     J = jacobian_csr(out, nx * ny * nz)
     delta = np.atleast_1d(spsolve(J.tocsc(), -out["R"]))
     return p + delta, delta, out["R"]
+
+
+def mesh_pattern(n, ci, cj):
+    """(row_ptr, col_idx, conn_of) of a connection list, columns ascending;
+    conn_of[e] is the connection of entry e (-1 on the diagonal)."""
+    lib = _load()
+    ci = np.ascontiguousarray(ci, dtype=np.int64)
+    cj = np.ascontiguousarray(cj, dtype=np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    L = ctypes.c_longlong
+    nnz = lib.orc_mesh_pattern(n, ci.size, _ptr(ci, L), _ptr(cj, L), _ptr(row_ptr, L), None, None)
+    if nnz < 0:
+        raise ValueError("bad connection list")
+    col_idx = np.zeros(nnz, dtype=np.int64)
+    conn_of = np.zeros(nnz, dtype=np.int64)
+    nnz = lib.orc_mesh_pattern(n, ci.size, _ptr(ci, L), _ptr(cj, L), _ptr(row_ptr, L), _ptr(col_idx, L),
+                               _ptr(conn_of, L))
+    if nnz < 0:
+        raise ValueError("bad connection list (duplicate pair)")
+    return row_ptr, col_idx, conn_of
+
+
+def mesh_assemble(n, phys, ci, cj, T, V, poro, depth, p, pn, pat=None, flip=None, want_links=False):
+    """R and CSR J of Eq. vk on a connection list (see ``assemble``)."""
+    lib = _load()
+    q = make_params(phys)
+    if pat is None:
+        pat = mesh_pattern(n, ci, cj)
+    row_ptr, col_idx, conn_of = pat
+    nnz = int(row_ptr[-1])
+    T = _f64(T).reshape(-1)
+    V, poro, depth, p, pn = (_f64(x).reshape(-1) for x in (V, poro, depth, p, pn))
+    for x in (V, poro, depth, p, pn):
+        assert x.size == n
+    R = np.zeros(n)
+    J = np.zeros(nnz)
+    F = np.zeros(nnz) if want_links else None
+    dphi = np.zeros(nnz) if want_links else None
+    acc = np.zeros(n) if want_links else None
+    fl = None
+    if flip is not None:
+        fl = np.ascontiguousarray(flip, dtype=np.uint8)
+        assert fl.size == nnz
+    D, L = ctypes.c_double, ctypes.c_longlong
+    rc = lib.orc_mesh_assemble(n, ctypes.byref(q), _ptr(T, D), _ptr(V, D), _ptr(poro, D), _ptr(depth, D),
+                               _ptr(p, D), _ptr(pn, D), _ptr(row_ptr, L), _ptr(col_idx, L), _ptr(conn_of, L),
+                               _ptr(fl, ctypes.c_ubyte), _ptr(R, D), _ptr(J, D), _ptr(F, D), _ptr(dphi, D),
+                               _ptr(acc, D))
+    if rc != 0:
+        raise ValueError("oracle mesh assemble failed")
+    out = {"R": R, "J": J, "row_ptr": row_ptr, "col_idx": col_idx, "conn_of": conn_of}
+    if want_links:
+        out.update(F=F, dphi=dphi, acc=acc)
+    return out
 
 
 def link_trans(phys, kK, kL, di, dj, dk):

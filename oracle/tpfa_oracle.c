@@ -200,15 +200,20 @@ static orc_conn orc_connection(const orc_params* q, double T, double pK, double 
  * (relative size c_f |p - p^n|, about 1e-5 here), so FP64 would lose about
  * eleven of its sixteen digits to cancellation; it is evaluated in long
  * double (80-bit or 128-bit) and rounded to double once. */
-static void orc_accumulation(const orc_params* q, double phi0, double p, double pn,
-                             double* A, double* dA) {
-    long double V = (long double)q->dx * q->dy * q->dz;
+static void orc_accumulation_v(const orc_params* q, long double V, double phi0, double p, double pn,
+                               double* A, double* dA) {
     long double rho = q->rho_ref * expl((long double)q->c_f * ((long double)p - q->p_ref));
     long double rhon = q->rho_ref * expl((long double)q->c_f * ((long double)pn - q->p_ref));
     long double phi = phi0 * (1.0L + (long double)q->c_r * ((long double)p - q->p_ref));
     long double phin = phi0 * (1.0L + (long double)q->c_r * ((long double)pn - q->p_ref));
     *A = (double)(V * (phi * rho - phin * rhon) / q->dt);
     *dA = (double)(V * (phi0 * q->c_r * rho + phi * q->c_f * rho) / q->dt);
+}
+
+/* The same for a cell of the structured grid, V = dx dy dz. */
+static void orc_accumulation(const orc_params* q, double phi0, double p, double pn,
+                             double* A, double* dA) {
+    orc_accumulation_v(q, (long double)q->dx * q->dy * q->dz, phi0, p, pn, A, dA);
 }
 
 /*
@@ -305,6 +310,115 @@ int orc_vjp(int nx, int ny, int nz, const orc_params* q,
         double A, dA;
         orc_accumulation(q, poro[K], p[K], pn[K], &A, &dA);
         g_p[K] += v[K] * dA;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * General meshes: a list of connections (K, L, Upsilon_KL) -- the form the
+ * paper names as its extension to arbitrary mesh topologies (Section 8).
+ * Each connection joins two distinct cells; adj(K) is every cell sharing a
+ * connection with K.  Upsilon is an input (a mesh generator computes it from
+ * the cell geometry), the cell volume V_K varies per cell, and the flux,
+ * upwinding, density and accumulation are those above.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Pattern of a connection list: row K holds K and every cell connected to
+ * it, columns ascending (insertion sort).  conn_of[e] is the connection of
+ * entry e (-1 on the diagonal).  With col_idx == NULL only row_ptr is filled.
+ * Returns nnz, or -1 for an index out of range, a connection of a cell with
+ * itself, or the same pair listed twice.
+ */
+long long orc_mesh_pattern(long long n, long long nc, const long long* ci, const long long* cj,
+                           long long* row_ptr, long long* col_idx, long long* conn_of) {
+    if (n <= 0 || nc < 0) return -1;
+    for (long long c = 0; c < nc; ++c)
+        if (ci[c] < 0 || ci[c] >= n || cj[c] < 0 || cj[c] >= n || ci[c] == cj[c]) return -1;
+    for (long long K = 0; K <= n; ++K) row_ptr[K] = 0;
+    for (long long c = 0; c < nc; ++c) {
+        row_ptr[ci[c] + 1] += 1;
+        row_ptr[cj[c] + 1] += 1;
+    }
+    for (long long K = 0; K < n; ++K) row_ptr[K + 1] += row_ptr[K] + 1; /* + 1: the diagonal */
+    long long nnz = row_ptr[n];
+    if (!col_idx) return nnz;
+    long long* fill = (long long*)malloc(sizeof(long long) * (size_t)n);
+    if (!fill) return -1;
+    for (long long K = 0; K < n; ++K) {
+        fill[K] = row_ptr[K] + 1;
+        col_idx[row_ptr[K]] = K;
+        conn_of[row_ptr[K]] = -1;
+    }
+    for (long long c = 0; c < nc; ++c) {
+        long long e = fill[ci[c]]++;
+        col_idx[e] = cj[c];
+        conn_of[e] = c;
+        e = fill[cj[c]]++;
+        col_idx[e] = ci[c];
+        conn_of[e] = c;
+    }
+    free(fill);
+    int dup = 0;
+    for (long long K = 0; K < n; ++K) { /* insertion sort of each row by column */
+        for (long long e = row_ptr[K] + 1; e < row_ptr[K + 1]; ++e) {
+            long long cv = col_idx[e], cc = conn_of[e], f = e - 1;
+            while (f >= row_ptr[K] && col_idx[f] > cv) {
+                col_idx[f + 1] = col_idx[f];
+                conn_of[f + 1] = conn_of[f];
+                --f;
+            }
+            col_idx[f + 1] = cv;
+            conn_of[f + 1] = cc;
+        }
+        for (long long e = row_ptr[K] + 1; e < row_ptr[K + 1]; ++e)
+            if (col_idx[e] == col_idx[e - 1]) dup = 1;
+    }
+    return dup ? -1 : nnz;
+}
+
+/*
+ * Residual and Jacobian of Eq. vk on a connection list, Algorithm 1's loops:
+ * for each cell K, for each L in adj(K) (row K of the pattern), the flux of
+ * connection (K, L) seen from K; then the accumulation term with V_K.
+ *   T, V        : nc transmissibilities, n cell volumes
+ *   poro, depth, p, pn, row_ptr, col_idx, conn_of : as orc_assemble / orc_mesh_pattern
+ *   flip, R, J, F_out, dphi_out, acc_out          : as orc_assemble
+ */
+int orc_mesh_assemble(long long n, const orc_params* q, const double* T, const double* V,
+                      const double* poro, const double* depth, const double* p, const double* pn,
+                      const long long* row_ptr, const long long* col_idx, const long long* conn_of,
+                      const unsigned char* flip, double* R, double* J, double* F_out, double* dphi_out,
+                      double* acc_out) {
+    if (n <= 0 || q == NULL || !(q->dt > 0.0) || !(q->mu > 0.0)) return -1;
+    long long nnz = row_ptr[n];
+    if (J) memset(J, 0, sizeof(double) * (size_t)nnz);
+    if (F_out) memset(F_out, 0, sizeof(double) * (size_t)nnz);
+    if (dphi_out) memset(dphi_out, 0, sizeof(double) * (size_t)nnz);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long long K = 0; K < n; ++K) {
+        double rK = 0.0;
+        long long dpos = orc_find(row_ptr, col_idx, K, K);
+        for (long long e = row_ptr[K]; e < row_ptr[K + 1]; ++e) {
+            long long L = col_idx[e];
+            if (L == K) continue;
+            int fl = flip ? flip[e] != 0 : 0;
+            orc_conn c = orc_connection(q, T[conn_of[e]], p[K], p[L], depth[K], depth[L], fl);
+            rK += c.F;
+            if (J) {
+                J[dpos] += c.dF_dpK;
+                J[e] = c.dF_dpL;
+            }
+            if (F_out) F_out[e] = c.F;
+            if (dphi_out) dphi_out[e] = c.dphi;
+        }
+        double A, dA;
+        orc_accumulation_v(q, (long double)V[K], poro[K], p[K], pn[K], &A, &dA);
+        if (R) R[K] = A + rK;
+        if (J) J[dpos] += dA;
+        if (acc_out) acc_out[K] = A;
     }
     return 0;
 }

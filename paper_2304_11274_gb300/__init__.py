@@ -9,7 +9,7 @@ __version__ = "1.0.0"
 
 
 def __getattr__(name):
-    if name in ("Grid", "TPFAError"):
+    if name in ("Grid", "Mesh", "Ensemble", "TPFAError"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

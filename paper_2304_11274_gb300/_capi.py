@@ -90,6 +90,14 @@ SIGNATURES = [
     ("tpfa_set_tiling", _I, [_VP, _I, _I]),
     ("tpfa_get_tiling", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("tpfa_autotune", _I, [_VP, ctypes.c_char_p, _VP]),
+    ("tpfa_create_mesh", _I, [ctypes.POINTER(_VP), _LL, _LL, ctypes.POINTER(TPFAParams), _I] + [_VP] * 7),
+    ("tpfa_mesh_set_state", _I, [_VP, _VP, _VP, _VP]),
+    ("tpfa_mesh_set_pressure", _I, [_VP, _VP]),
+    ("tpfa_mesh_assemble", _I, [_VP, _VP, _VP, _VP, _VP]),
+    ("tpfa_mesh_copy_pattern", _I, [_VP, _VP, _VP, _VP]),
+    ("tpfa_mesh_info", _I, [_VP] + [ctypes.POINTER(_LL)] * 3 + [ctypes.POINTER(_I)]),
+    ("tpfa_mesh_sync_status", _I, [_VP, _VP]),
+    ("tpfa_destroy_mesh", _I, [_VP]),
     ("tpfa_create_ensemble", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)]),
     ("tpfa_ensemble_set_outputs", _I, [_VP, _I, _VP, _VP, _VP]),
     ("tpfa_assemble_batch", _I, [_VP, _VP]),

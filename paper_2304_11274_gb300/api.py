@@ -29,6 +29,12 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _unused_mesh_params() -> dict:
+    """Placeholders for the parameters a mesh does not use (cell sizes and
+    connectivity), so that a mesh's physics dict may omit them."""
+    return {"dx": 1.0, "dy": 1.0, "dz": 1.0, "connectivity": 6}
+
+
 def params_struct(phys: dict) -> _capi.TPFAParams:
     return _capi.TPFAParams(**{k: phys[k] for k, _ in _capi.TPFAParams._fields_})
 
@@ -308,6 +314,106 @@ class Ensemble:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Mesh:
+    """A general mesh given as a connection list (cells ci[c], cj[c] joined by
+    transmissibility T[c]) with per-cell volume, porosity and depth; the
+    residual and Jacobian of Eq. vk on it, on the GPU.
+
+    n           : number of cells
+    ci, cj, T   : connection list (int cell indices, m^3 transmissibilities)
+    V, poro, depth : per-cell fields (m^3, -, m positive down)
+    phys        : dict of rho_ref, p_ref, c_f, mu, g, dt, c_r (cell sizes and
+                  connectivity are not used)
+    precision   : "mixed" or "fp64"
+    """
+
+    def __init__(self, n, ci, cj, T, V, poro, depth, phys, precision="mixed", device="cuda"):
+        self.lib = _capi.load()
+        self.n = int(n)
+        self.phys = dict(phys)
+        self.precision = precision
+        self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.float32 if precision == "mixed" else torch.float64
+        prm = params_struct({**_unused_mesh_params(), **self.phys})
+        with torch.cuda.device(self.device):
+            a = torch.as_tensor(np.ascontiguousarray(ci, dtype=np.int32), device=self.device)
+            b = torch.as_tensor(np.ascontiguousarray(cj, dtype=np.int32), device=self.device)
+            t = _dev_f64(T, self.device)
+            v, ph, z = (_dev_f64(x, self.device) for x in (V, poro, depth))
+            if not (a.numel() == b.numel() == t.numel()):
+                raise ValueError("ci, cj and T must have the same length")
+            h = ctypes.c_void_p()
+            check(self.lib.tpfa_create_mesh(ctypes.byref(h), self.n, a.numel(), ctypes.byref(prm),
+                                            PRECISIONS[precision], _ptr(a), _ptr(b), _ptr(t), _ptr(v), _ptr(ph),
+                                            _ptr(z), _stream()))
+        self.handle = h
+        nnz, nc = ctypes.c_longlong(), ctypes.c_longlong()
+        check(self.lib.tpfa_mesh_info(h, None, ctypes.byref(nc), ctypes.byref(nnz), None))
+        self.nnz, self.nc = int(nnz.value), int(nc.value)
+        self._p = self._pn = None
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.tpfa_destroy_mesh(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    _field = Grid._field
+
+    def set_state(self, p, pn, stream=None):
+        p, pn = self._field(p), self._field(pn)
+        check(self.lib.tpfa_mesh_set_state(self.handle, _ptr(p), _ptr(pn), _stream(stream)))
+        self._p, self._pn = p, pn
+
+    def set_pressure(self, p):
+        p = self._field(p)
+        check(self.lib.tpfa_mesh_set_pressure(self.handle, _ptr(p)))
+        self._p = p
+
+    def empty_outputs(self):
+        R = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        vals = torch.empty(self.nnz, dtype=self.dtype, device=self.device)
+        diag = torch.empty(self.n, dtype=torch.float64, device=self.device) if self.precision == "mixed" else None
+        return R, vals, diag
+
+    def assemble(self, R=None, vals=None, diag=None, want_residual=True, stream=None):
+        """Fused residual + Jacobian: (R, vals, diag64), CSR order of pattern()."""
+        if vals is None:
+            R0, vals, diag0 = self.empty_outputs()
+            R = R if R is not None else (R0 if want_residual else None)
+            diag = diag if diag is not None else diag0
+        check(self.lib.tpfa_mesh_assemble(self.handle, _ptr(R), _ptr(vals), _ptr(diag), _stream(stream)))
+        return R, vals, diag
+
+    def assemble_residual(self, R=None, stream=None):
+        if R is None:
+            R = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        check(self.lib.tpfa_mesh_assemble(self.handle, _ptr(R), None, None, _stream(stream)))
+        return R
+
+    def pattern(self, stream=None):
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        ci = torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        check(self.lib.tpfa_mesh_copy_pattern(self.handle, _ptr(rp), _ptr(ci), _stream(stream)))
+        return rp, ci
+
+    def sync_status(self, stream=None):
+        check(self.lib.tpfa_mesh_sync_status(self.handle, _stream(stream)))
 
 
 class TPFAResidual(torch.autograd.Function):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtpfa.so")
 OBJDIR = os.path.join(ROOT, "_build")
-SOURCES = ["tpfa_api.cu", "tpfa_setup.cu", "tpfa_assemble.cu", "tpfa_static.cu", "tpfa_vjp.cu", "tpfa_jvp.cu", "tpfa_krylov.cu", "tpfa_batch.cu"]
+SOURCES = ["tpfa_api.cu", "tpfa_setup.cu", "tpfa_assemble.cu", "tpfa_static.cu", "tpfa_vjp.cu", "tpfa_jvp.cu", "tpfa_krylov.cu", "tpfa_mesh.cu", "tpfa_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

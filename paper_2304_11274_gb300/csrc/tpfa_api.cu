@@ -11,6 +11,8 @@
 
 #include <algorithm>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "tpfa_common.cuh"
 #include "tpfa_impl.h"
@@ -275,6 +277,115 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     if (!converged)
         return fail(TPFA_ERR_NO_CONVERGENCE, "BiCGStab stopped after %d iterations at relative residual %.3e%s",
                     Sh->iter, Sh->bb > 0.0 ? sqrt(Sh->rr / Sh->bb) : 0.0, Sh->breakdown ? " (breakdown)" : "");
+    return TPFA_OK;
+}
+
+}  // namespace
+
+// A general mesh: the pattern built from the connection list, per-entry
+// transmissibilities, cell fields and the bound state.
+struct tpfa_mesh_s {
+    int device = 0;
+    long long N = 0, nc = 0, nnz = 0;
+    tpfa_precision prec = TPFA_MIXED;
+    PhysF qf{};
+    PhysD qd{};
+    SetupPhys sp{};
+    bool crk = false;
+    size_t real_size = 4;
+    long long* row_ptr = nullptr;
+    int* col_idx = nullptr;
+    void* Tc = nullptr;
+    void* z = nullptr;
+    double* vphi_d = nullptr;
+    void* vphi_r = nullptr;
+    double* mn = nullptr;
+    unsigned int* status = nullptr;
+    const void* p = nullptr;
+    const void* pn = nullptr;
+    bool has_state = false;
+
+    void release() {
+        dev_free(row_ptr);
+        dev_free(col_idx);
+        dev_free(Tc);
+        dev_free(z);
+        dev_free(vphi_d);
+        dev_free(vphi_r);
+        dev_free(mn);
+        dev_free(status);
+        row_ptr = nullptr, col_idx = nullptr, Tc = nullptr, z = nullptr, vphi_d = nullptr, vphi_r = nullptr;
+        mn = nullptr, status = nullptr;
+    }
+};
+
+namespace {
+
+template <typename Real>
+MeshFields<Real> mesh_fields(const tpfa_mesh_s* m) {
+    MeshFields<Real> f;
+    f.row_ptr = m->row_ptr;
+    f.col = m->col_idx;
+    f.Tc = static_cast<const Real*>(m->Tc);
+    f.p = static_cast<const Real*>(m->p);
+    f.pn = static_cast<const Real*>(m->pn);
+    f.mn = m->mn;
+    f.z = static_cast<const Real*>(m->z);
+    f.phi0 = static_cast<const Real*>(m->vphi_r ? m->vphi_r : m->z);  // never NULL; read only when c_r != 0
+    return f;
+}
+
+// Host-side CSR of a connection list: row K = K and its neighbours, columns
+// ascending; Tc[e] the entry's transmissibility (0 on the diagonal).
+int build_mesh_pattern(long long n, long long nc, const std::vector<int>& ci, const std::vector<int>& cj,
+                       const std::vector<double>& T, std::vector<long long>& row_ptr, std::vector<int>& col,
+                       std::vector<double>& Tc) {
+    for (long long c = 0; c < nc; ++c) {
+        if (ci[c] < 0 || ci[c] >= n || cj[c] < 0 || cj[c] >= n)
+            return fail(TPFA_ERR_INVALID_ARG, "connection %lld joins cells %d and %d outside [0, %lld)", c, ci[c],
+                        cj[c], n);
+        if (ci[c] == cj[c]) return fail(TPFA_ERR_INVALID_ARG, "connection %lld joins cell %d to itself", c, ci[c]);
+        if (!(T[c] >= 0.0) || !(T[c] < 1e300))
+            return fail(TPFA_ERR_INVALID_ARG, "connection %lld has transmissibility %g", c, T[c]);
+    }
+    row_ptr.assign(n + 1, 0);
+    for (long long c = 0; c < nc; ++c) {
+        row_ptr[ci[c] + 1] += 1;
+        row_ptr[cj[c] + 1] += 1;
+    }
+    for (long long K = 0; K < n; ++K) row_ptr[K + 1] += row_ptr[K] + 1;
+    const long long nnz = row_ptr[n];
+    if (nnz >= (1LL << 31)) return fail(TPFA_ERR_TOO_LARGE, "the pattern has %lld entries (>= 2^31)", nnz);
+    col.assign(nnz, 0);
+    Tc.assign(nnz, 0.0);
+    std::vector<long long> fill(n);
+    for (long long K = 0; K < n; ++K) {
+        col[row_ptr[K]] = (int)K;
+        fill[K] = row_ptr[K] + 1;
+    }
+    for (long long c = 0; c < nc; ++c) {
+        long long e = fill[ci[c]]++;
+        col[e] = cj[c];
+        Tc[e] = T[c];
+        e = fill[cj[c]]++;
+        col[e] = ci[c];
+        Tc[e] = T[c];
+    }
+    std::vector<std::pair<int, double>> row;
+    for (long long K = 0; K < n; ++K) {
+        const long long a = row_ptr[K], b = row_ptr[K + 1];
+        row.clear();
+        for (long long e = a; e < b; ++e) row.emplace_back(col[e], Tc[e]);
+        std::sort(row.begin(), row.end(), [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+            return x.first < y.first;
+        });
+        for (long long e = a; e < b; ++e) {
+            col[e] = row[e - a].first;
+            Tc[e] = row[e - a].second;
+            if (e > a && col[e] == col[e - 1])
+                return fail(TPFA_ERR_INVALID_ARG, "cells %lld and %d are connected more than once", K, col[e]);
+        }
+    }
     return TPFA_OK;
 }
 
@@ -659,6 +770,191 @@ int tpfa_destroy(tpfa_handle h) {
         h->release();
     }
     delete h;
+    return TPFA_OK;
+}
+
+int tpfa_create_mesh(tpfa_mesh* out, long long n_cells, long long n_conn, const tpfa_params* prm,
+                     tpfa_precision prec, const int* conn_i_dev, const int* conn_j_dev, const double* trans_dev,
+                     const double* volume_dev, const double* poro_dev, const double* depth_dev, void* stream) {
+    g_err.clear();
+    if (!out) return fail(TPFA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_cells < 1) return fail(TPFA_ERR_INVALID_ARG, "a mesh needs at least one cell");
+    if (n_cells >= (1LL << 31)) return fail(TPFA_ERR_TOO_LARGE, "%lld cells exceed 2^31 - 1", n_cells);
+    if (n_conn < 0) return fail(TPFA_ERR_INVALID_ARG, "negative connection count");
+    if (!prm) return fail(TPFA_ERR_INVALID_ARG, "params is NULL");
+    if (!(prm->mu > 0.0) || !(prm->dt > 0.0)) return fail(TPFA_ERR_INVALID_ARG, "mu and dt must be > 0");
+    if (prec != TPFA_FP64 && prec != TPFA_MIXED) return fail(TPFA_ERR_INVALID_ARG, "bad precision %d", (int)prec);
+    if (!volume_dev || !poro_dev || !depth_dev || (n_conn > 0 && (!conn_i_dev || !conn_j_dev || !trans_dev)))
+        return fail(TPFA_ERR_INVALID_ARG, "mesh arrays must be non-NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // the connection list comes to the host once for the pattern build
+    std::vector<int> ci(n_conn), cj(n_conn);
+    std::vector<double> T(n_conn);
+    if (n_conn > 0) {
+        e = cudaMemcpyAsync(ci.data(), conn_i_dev, sizeof(int) * n_conn, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cj.data(), conn_j_dev, sizeof(int) * n_conn, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(T.data(), trans_dev, sizeof(double) * n_conn, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "connection list download");
+    }
+    std::vector<long long> row_ptr;
+    std::vector<int> col;
+    std::vector<double> Tc;
+    int rc = build_mesh_pattern(n_cells, n_conn, ci, cj, T, row_ptr, col, Tc);
+    if (rc) return rc;
+
+    tpfa_mesh_s* m = new tpfa_mesh_s();
+    m->device = dev;
+    m->N = n_cells;
+    m->nc = n_conn;
+    m->nnz = row_ptr[n_cells];
+    m->prec = prec;
+    m->crk = prm->c_r != 0.0;
+    m->real_size = prec == TPFA_MIXED ? sizeof(float) : sizeof(double);
+    // the cell volume is folded into m^n and into (V/dt) phi0, so V_dt = 1
+    m->qd = PhysD{prm->rho_ref, prm->p_ref, prm->c_f, 1.0 / prm->mu, prm->g, 0.5 * prm->g, 1.0, prm->c_r};
+    m->qf = PhysF{(float)prm->rho_ref, (float)prm->p_ref, (float)prm->c_f, (float)(1.0 / prm->mu), (float)prm->g,
+                  (float)(0.5 * prm->g), 1.0f, (float)prm->c_r};
+    m->sp = SetupPhys{1.0, 1.0, 1.0, prm->rho_ref, prm->p_ref, prm->c_f, prm->c_r, 1.0};
+    const size_t rb = m->real_size * (size_t)n_cells;
+    double* Tc_d = nullptr;
+    bool ok = dev_alloc((void**)&m->row_ptr, sizeof(long long) * (size_t)(n_cells + 1)) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&m->col_idx, sizeof(int) * (size_t)m->nnz) == cudaSuccess;
+    ok = ok && dev_alloc(&m->Tc, m->real_size * (size_t)m->nnz) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&Tc_d, sizeof(double) * (size_t)m->nnz) == cudaSuccess;
+    ok = ok && dev_alloc(&m->z, rb) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&m->vphi_d, sizeof(double) * (size_t)n_cells) == cudaSuccess;
+    if (ok && m->crk) ok = dev_alloc(&m->vphi_r, rb) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&m->mn, sizeof(double) * (size_t)n_cells) == cudaSuccess;
+    ok = ok && dev_alloc((void**)&m->status, sizeof(unsigned int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        dev_free(Tc_d);
+        m->release();
+        delete m;
+        return fail(TPFA_ERR_OOM, "device allocation failed for a mesh of %lld cells", n_cells);
+    }
+    e = cudaMemcpyAsync(m->row_ptr, row_ptr.data(), sizeof(long long) * (n_cells + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->col_idx, col.data(), sizeof(int) * m->nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Tc_d, Tc.data(), sizeof(double) * m->nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        if (prec == TPFA_MIXED) {
+            e = launch_convert_f32(Tc_d, (float*)m->Tc, m->nnz, st);
+            if (e == cudaSuccess) e = launch_convert_f32(depth_dev, (float*)m->z, n_cells, st);
+        } else {
+            e = launch_copy_f64(Tc_d, (double*)m->Tc, m->nnz, st);
+            if (e == cudaSuccess) e = launch_copy_f64(depth_dev, (double*)m->z, n_cells, st);
+        }
+    }
+    if (e == cudaSuccess)
+        e = launch_mesh_vphi(n_cells, prm->dt, prec == TPFA_MIXED, volume_dev, poro_dev, m->vphi_d, m->vphi_r, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(Tc_d);
+    if (e != cudaSuccess) {
+        m->release();
+        delete m;
+        return cuda_fail(e, "mesh setup");
+    }
+    *out = m;
+    return TPFA_OK;
+}
+
+int tpfa_mesh_set_state(tpfa_mesh m, const void* p_dev, const void* p_prev_dev, void* stream) {
+    if (!m) return fail(TPFA_ERR_INVALID_ARG, "mesh is NULL");
+    if (!p_dev || !p_prev_dev) return fail(TPFA_ERR_INVALID_ARG, "p and p_prev must be non-NULL");
+    DeviceGuard dg(m->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = m->prec == TPFA_MIXED
+                        ? launch_prev_mass_f32(m->sp, (const float*)p_prev_dev, m->vphi_d, m->mn, m->N, st)
+                        : launch_prev_mass_f64(m->sp, (const double*)p_prev_dev, m->vphi_d, m->mn, m->N, st);
+    if (e != cudaSuccess) return cuda_fail(e, "previous-step mass");
+    m->p = p_dev;
+    m->pn = p_prev_dev;
+    m->has_state = true;
+    return TPFA_OK;
+}
+
+int tpfa_mesh_set_pressure(tpfa_mesh m, const void* p_dev) {
+    if (!m) return fail(TPFA_ERR_INVALID_ARG, "mesh is NULL");
+    if (!p_dev) return fail(TPFA_ERR_INVALID_ARG, "p must be non-NULL");
+    if (!m->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_mesh_set_state has not been called");
+    m->p = p_dev;
+    return TPFA_OK;
+}
+
+int tpfa_mesh_assemble(tpfa_mesh m, double* R_dev, void* vals_dev, double* diag64_dev, void* stream) {
+    if (!m) return fail(TPFA_ERR_INVALID_ARG, "mesh is NULL");
+    if (!R_dev && !vals_dev) return fail(TPFA_ERR_INVALID_ARG, "nothing to assemble (R and vals NULL)");
+    if (m->prec == TPFA_FP64 && diag64_dev) return fail(TPFA_ERR_INVALID_ARG, "diag64 must be NULL on the FP64 path");
+    if (!m->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_mesh_set_state has not been called");
+    DeviceGuard dg(m->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (m->prec == TPFA_MIXED) {
+        AsmOut<float> o{R_dev, static_cast<float*>(vals_dev), diag64_dev, m->status};
+        e = launch_mesh_mixed(mesh_fields<float>(m), m->N, m->qf, m->crk, o, st);
+    } else {
+        AsmOut<double> o{R_dev, static_cast<double*>(vals_dev), nullptr, m->status};
+        e = launch_mesh_fp64(mesh_fields<double>(m), m->N, m->qd, m->crk, o, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mesh assembly launch");
+    return TPFA_OK;
+}
+
+int tpfa_mesh_copy_pattern(tpfa_mesh m, long long* row_ptr_out_dev, int* col_idx_out_dev, void* stream) {
+    if (!m) return fail(TPFA_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (row_ptr_out_dev)
+        e = cudaMemcpyAsync(row_ptr_out_dev, m->row_ptr, sizeof(long long) * (size_t)(m->N + 1),
+                            cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && col_idx_out_dev)
+        e = cudaMemcpyAsync(col_idx_out_dev, m->col_idx, sizeof(int) * (size_t)m->nnz, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pattern copy");
+    return TPFA_OK;
+}
+
+int tpfa_mesh_info(tpfa_mesh m, long long* n_cells, long long* n_conn, long long* nnz, int* precision) {
+    if (!m) return fail(TPFA_ERR_INVALID_ARG, "mesh is NULL");
+    if (n_cells) *n_cells = m->N;
+    if (n_conn) *n_conn = m->nc;
+    if (nnz) *nnz = m->nnz;
+    if (precision) *precision = (int)m->prec;
+    return TPFA_OK;
+}
+
+int tpfa_mesh_sync_status(tpfa_mesh m, void* stream) {
+    if (!m) return fail(TPFA_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int s = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&s, m->status, sizeof s, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && s) e = cudaMemset(m->status, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (s & STATUS_DEVICE_CHECK) return fail(TPFA_ERR_DEVICE_CHECK, "a device-side bounds check failed");
+    if (s & STATUS_NONFINITE) return fail(TPFA_ERR_NONFINITE, "a residual or Jacobian value was NaN or Inf");
+    return TPFA_OK;
+}
+
+int tpfa_destroy_mesh(tpfa_mesh m) {
+    if (!m) return TPFA_OK;
+    {
+        DeviceGuard dg(m->device);
+        cudaDeviceSynchronize();
+        m->release();
+    }
+    delete m;
     return TPFA_OK;
 }
 

@@ -5,6 +5,7 @@
 
 #include "../../include/tpfa.h"
 #include "tpfa_grid.h"
+#include "tpfa_mesh.h"
 
 namespace tpfa {
 
@@ -79,6 +80,14 @@ cudaError_t krylov_start(const GridGeom& g, long long n, const double* b, double
 cudaError_t krylov_iteration(const GridGeom& g, long long n, bool mixed, const void* vals, const double* diag64,
                              const KrylovWork& w, cudaStream_t st);
 cudaError_t krylov_add_delta(long long n, bool mixed, void* p, const double* d, cudaStream_t st);
+
+// General meshes (tpfa_mesh.cu).
+cudaError_t launch_mesh_vphi(long long n, double dt, bool mixed, const double* V, const double* poro,
+                             double* vphi_d, void* vphi_r, cudaStream_t st);
+cudaError_t launch_mesh_mixed(const MeshFields<float>& f, long long n, const PhysF& q, bool crk,
+                              const AsmOut<float>& o, cudaStream_t st);
+cudaError_t launch_mesh_fp64(const MeshFields<double>& f, long long n, const PhysD& q, bool crk,
+                             const AsmOut<double>& o, cudaStream_t st);
 
 // Sets the thread-local message of tpfa_last_error_string and returns code.
 int report_error(int code, const char* msg);

@@ -126,6 +126,99 @@ def round_to_f32(prob: Problem) -> Problem:
     return dataclasses.replace(prob, p=r(prob.p), pn=r(prob.pn), depth=r(prob.depth))
 
 
+# ---------------------------------------------------------------- general meshes
+
+
+@dataclasses.dataclass
+class Mesh:
+    """A mesh given as a connection list (cell indices ci[c], cj[c] and the
+    transmissibility T[c] of connection c) with per-cell fields."""
+    n: int
+    phys: dict
+    ci: np.ndarray     # (nc,) int64
+    cj: np.ndarray     # (nc,) int64
+    T: np.ndarray      # (nc,) float64, m^3
+    V: np.ndarray      # (n,) float64, m^3
+    poro: np.ndarray
+    depth: np.ndarray
+    p: np.ndarray
+    pn: np.ndarray
+
+    @property
+    def nc(self) -> int:
+        return int(self.ci.size)
+
+
+def structured_pairs(nx, ny, nz, connectivity):
+    """Cell pairs of a structured grid's links, each listed once from its
+    owner: +x, +y, +z, and with 10 links (+x,+y) and (-x,+y).  Returns linear
+    indices (a, b) and the link kind 0..4 in that order.  Topology only."""
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="xy")
+    i, j, k = (np.moveaxis(x, 2, 0).reshape(-1) for x in (i, j, k))
+    lin = i + nx * (j + ny * k)
+    out_a, out_b, out_k = [], [], []
+    steps = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    if connectivity == 10:
+        steps += [(1, 1, 0), (-1, 1, 0)]
+    for kind, (di, dj, dk) in enumerate(steps):
+        ok = (i + di >= 0) & (i + di < nx) & (j + dj < ny) & (k + dk < nz)
+        out_a.append(lin[ok])
+        out_b.append((i + di + nx * (j + dj + ny * (k + dk)))[ok])
+        out_k.append(np.full(int(ok.sum()), kind))
+    return np.concatenate(out_a), np.concatenate(out_b), np.concatenate(out_k)
+
+
+def make_mesh(nx, ny, nz, seed, *, connectivity=6, fault=True, inactive=0.05, perturb=1.0e5, **phys_over) -> Mesh:
+    """A corner-point-like mesh with a fault, the kind of topology the paper
+    defers to future work: the cells of a structured nx x ny x nz grid, the
+    block x >= nx/2 thrown down by half a layer (so the faces across the
+    fault become two non-neighbour connections per cell, to the cells at the
+    same and at the next shallower layer), a fraction of inactive (pinched-
+    out) cells removed with their connections, and per-cell volumes varying
+    by +-20 %.  Transmissibilities are drawn directly, log10 T ~ N(-12.7, 0.5)
+    m^3 (the magnitude of a 1e-13 m^2 face of 10 x 10 x 2 m cells); the rest
+    follows make_problem's distributions.  Active cells keep the structured
+    (x fastest) order."""
+    rng = np.random.default_rng(seed)
+    phys = physics(connectivity=connectivity, **phys_over)
+    dz = phys["dz"]
+    N = nx * ny * nz
+    i = np.tile(np.arange(nx), ny * nz)
+    k = np.repeat(np.arange(nz), nx * ny)
+    xf = nx // 2 if (fault and nx >= 2) else nx
+    depth_all = (k + 0.5) * dz + np.where(i >= xf, 0.5 * dz, 0.0)
+    a, b, kind = structured_pairs(nx, ny, nz, connectivity)
+    if xf < nx:
+        ia, ib = a % nx, b % nx
+        crosses = (np.minimum(ia, ib) < xf) & (np.maximum(ia, ib) >= xf)
+        a, b = a[~crosses], b[~crosses]
+        left = np.flatnonzero(i == xf - 1)
+        a = np.concatenate([a, left, left[k[left] >= 1]])
+        b = np.concatenate([b, left + 1, left[k[left] >= 1] + 1 - nx * ny])
+    active = rng.random(N) >= inactive
+    if not active.any():
+        active[0] = True
+    keep = active[a] & active[b]
+    a, b = a[keep], b[keep]
+    idx = np.cumsum(active) - 1
+    ci, cj = idx[a].astype(np.int64), idx[b].astype(np.int64)
+    n = int(active.sum())
+    T = np.power(10.0, rng.normal(-12.7, 0.5, size=ci.size))
+    V = phys["dx"] * phys["dy"] * dz * rng.uniform(0.8, 1.2, size=n)
+    poro = rng.uniform(0.1, 0.3, size=n)
+    depth = depth_all[active]
+    base = 1.0e7 + phys["rho_ref"] * phys["g"] * (depth - 0.5 * dz)
+    p = base + rng.uniform(-perturb, perturb, size=n)
+    return Mesh(n, phys, ci, cj, T, V, poro, depth, p, base.copy())
+
+
+def round_mesh_to_f32(m: Mesh) -> Mesh:
+    """The mesh with the fields the mixed path stores in FP32 (pressure,
+    depth, transmissibility) rounded to FP32 and widened back."""
+    r = lambda x: x.astype(np.float32).astype(np.float64)
+    return dataclasses.replace(m, p=r(m.p), pn=r(m.pn), depth=r(m.depth), T=r(m.T))
+
+
 # The five workloads: (nx, ny, nz, connectivity, precision, extra).
 CONFIGS = {
     0: dict(shape=(32, 32, 32), connectivity=6, precision="fp64", layered=False),

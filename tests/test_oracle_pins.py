@@ -495,6 +495,115 @@ def test_newton_converges_superlinearly():
     assert r[1] < 0.2 * r[0] or norms[2] <= 1e-12 * norms[0]
 
 
+# ---------------------------------------------------------------- general meshes
+
+_KIND_OFFSETS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (-1, 1, 0)]
+
+
+def _structured_as_mesh(pr):
+    """The structured problem pr as a connection list: its links, each
+    transmissibility from the oracle's two-point formula, V = dx dy dz."""
+    a, b, kind = synth.structured_pairs(pr.nx, pr.ny, pr.nz, pr.phys["connectivity"])
+    T = np.array([oracle.link_trans(pr.phys, pr.perm[x], pr.perm[y], *_KIND_OFFSETS[t])
+                  for x, y, t in zip(a, b, kind)])
+    V = np.full(pr.n, pr.phys["dx"] * pr.phys["dy"] * pr.phys["dz"])
+    return a, b, T, V
+
+
+@pytest.mark.parametrize("conn", [6, 10])
+def test_mesh_of_structured_grid_matches_structured_oracle(conn):
+    """A structured grid given as a connection list: the mesh pattern is the
+    structured pattern and R, J agree with the structured oracle (two
+    separate codes: adjacency from the list vs. Section 5.1's offsets)."""
+    pr = synth.make_problem(5, 4, 3, seed=51, connectivity=conn, c_r=1e-9)
+    a, b, T, V = _structured_as_mesh(pr)
+    ref = oracle.assemble(pr.nx, pr.ny, pr.nz, pr.phys, pr.perm, pr.poro, pr.depth, pr.p, pr.pn)
+    out = oracle.mesh_assemble(pr.n, pr.phys, a, b, T, V, pr.poro, pr.depth, pr.p, pr.pn)
+    assert np.array_equal(out["row_ptr"], ref["row_ptr"]) and np.array_equal(out["col_idx"], ref["col_idx"])
+    assert np.abs(out["R"] - ref["R"]).max() <= 1e-13 * np.abs(ref["R"]).max()
+    assert np.abs(out["J"] - ref["J"]).max() <= 1e-13 * np.abs(ref["J"]).max()
+
+
+def test_mesh_pattern_matches_bruteforce():
+    m = synth.make_mesh(7, 5, 4, seed=52, connectivity=10)
+    rp, ci, co = oracle.mesh_pattern(m.n, m.ci, m.cj)
+    A = np.eye(m.n, dtype=bool)
+    A[m.ci, m.cj] = True
+    A[m.cj, m.ci] = True
+    for K in range(m.n):
+        assert list(ci[rp[K]:rp[K + 1]]) == list(np.flatnonzero(A[K]))
+        for e in range(rp[K], rp[K + 1]):
+            c = co[e]
+            assert (c == -1) == (ci[e] == K)
+            if c >= 0:
+                assert {int(m.ci[c]), int(m.cj[c])} == {K, int(ci[e])}
+
+
+def test_mesh_rejects_bad_connection_lists():
+    with pytest.raises(ValueError):
+        oracle.mesh_pattern(3, [0, 1], [1, 1])  # a cell joined to itself
+    with pytest.raises(ValueError):
+        oracle.mesh_pattern(3, [0, 1], [1, 0])  # the same pair twice
+    with pytest.raises(ValueError):
+        oracle.mesh_pattern(3, [0], [3])  # out of range
+
+
+def test_mesh_fluxes_antisymmetric_and_conservative():
+    m = synth.make_mesh(8, 6, 5, seed=53, connectivity=10, c_r=1e-9)
+    out = oracle.mesh_assemble(m.n, m.phys, m.ci, m.cj, m.T, m.V, m.poro, m.depth, m.p, m.pn, want_links=True)
+    rp, ci, F, dphi = out["row_ptr"], out["col_idx"], out["F"], out["dphi"]
+    pos = {}
+    for K in range(m.n):
+        for e in range(rp[K], rp[K + 1]):
+            pos[(K, int(ci[e]))] = e
+    for (K, L), e in pos.items():
+        if K != L and dphi[e] != 0.0:
+            assert F[e] == -F[pos[(L, K)]]
+    flux = out["R"] - out["acc"]
+    assert abs(flux.sum()) <= 1e-12 * np.abs(F).sum()
+
+
+def test_mesh_jacobian_matches_central_differences():
+    m = synth.make_mesh(5, 4, 3, seed=54, connectivity=6, c_r=2e-9, c_f=3e-9)
+    base = oracle.mesh_assemble(m.n, m.phys, m.ci, m.cj, m.T, m.V, m.poro, m.depth, m.p, m.pn, want_links=True)
+    J = dense(base, m.n)
+    rp, ci, dphi = base["row_ptr"], base["col_idx"], base["dphi"]
+    compared = 0
+    for jcol in range(m.n):
+        h = 1e-6 * abs(m.p[jcol])
+        pp, pm = m.p.copy(), m.p.copy()
+        pp[jcol] += h
+        pm[jcol] -= h
+        Rp = oracle.mesh_assemble(m.n, m.phys, m.ci, m.cj, m.T, m.V, m.poro, m.depth, pp, m.pn)["R"]
+        Rm = oracle.mesh_assemble(m.n, m.phys, m.ci, m.cj, m.T, m.V, m.poro, m.depth, pm, m.pn)["R"]
+        fd = (Rp - Rm) / (2 * h)
+        for r in range(m.n):
+            row = slice(rp[r], rp[r + 1])
+            if np.any((np.abs(dphi[row]) < 4 * h) & (ci[row] != r)):
+                continue
+            assert abs(fd[r] - J[r, jcol]) <= 1e-6 * np.abs(J[r]).max(), (r, jcol)
+            compared += 1
+    assert compared > m.n * m.n // 2
+
+
+def test_mesh_two_cells_hand_derivation():
+    """Two cells, one connection, no gravity, c_r = 0: R_0 = A_0 + T rho_up/mu (p0 - p1)."""
+    phys = synth.physics(g=0.0, c_r=0.0)
+    p = np.array([1.02e7, 1.0e7])
+    pn = np.array([1.0e7, 1.0e7])
+    T, V, poro = 3e-13, np.array([150.0, 250.0]), np.array([0.2, 0.25])
+    out = oracle.mesh_assemble(2, phys, [0], [1], [T], V, poro, np.array([1.0, 1.0]), p, pn)
+    rho = phys["rho_ref"] * np.exp(phys["c_f"] * (p - phys["p_ref"]))
+    rhon = phys["rho_ref"] * np.exp(phys["c_f"] * (pn - phys["p_ref"]))
+    F = T * rho[0] / phys["mu"] * (p[0] - p[1])  # cell 0 is upstream
+    A = V * poro * (rho - rhon) / phys["dt"]
+    assert out["R"][0] == pytest.approx(A[0] + F, rel=1e-12)
+    assert out["R"][1] == pytest.approx(A[1] - F, rel=1e-12)
+    dF0 = T / phys["mu"] * (phys["c_f"] * rho[0] * (p[0] - p[1]) + rho[0])
+    assert out["J"][0] == pytest.approx(dF0 + V[0] * poro[0] * phys["c_f"] * rho[0] / phys["dt"], rel=1e-12)
+    assert out["J"][1] == pytest.approx(-T * rho[0] / phys["mu"], rel=1e-12)
+
+
 def test_upwind_tie_takes_the_neighbour():
     """Section 3's upwind rule picks rho_K only when dPhi_KL > 0 and the
     neighbour's density otherwise, so at an exact tie each row uses the OTHER
