@@ -108,6 +108,10 @@ struct tpfa_grid {
     double* h_R = nullptr;
     void* h_vals = nullptr;
     double* h_diag = nullptr;
+    // the host-buffer pipeline's copy streams and per-slab events
+    static constexpr int kMaxSlabs = 16;
+    cudaStream_t h_up = nullptr, h_down = nullptr;
+    cudaEvent_t h_ev[2 * kMaxSlabs + 2] = {};
     // Newton / Krylov workspace, allocated on first use
     void* kv_vals = nullptr;
     double* kv_diag = nullptr;
@@ -118,6 +122,13 @@ struct tpfa_grid {
     KrylovScalars* kv_S_host = nullptr;  // pinned
 
     void release() {
+        for (auto& ev : h_ev) {
+            if (ev) cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+        if (h_up) cudaStreamDestroy(h_up);
+        if (h_down) cudaStreamDestroy(h_down);
+        h_up = h_down = nullptr;
         dev_free(kv_vals);
         dev_free(kv_diag);
         dev_free(kv_R);
@@ -179,14 +190,15 @@ AsmFields<Real> fields_of(const tpfa_grid* h) {
     return f;
 }
 
-int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st) {
+int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st, int k0 = 0,
+           int k1 = -1) {
     cudaError_t e;
     if (h->prec == TPFA_MIXED) {
         AsmOut<float> o{R, static_cast<float*>(vals), diag64, h->status};
-        e = launch_assemble_mixed(kern, h->geom, h->qf, h->crk, fields_of<float>(h), o, h->JY, h->W, st);
+        e = launch_assemble_mixed(kern, h->geom, h->qf, h->crk, fields_of<float>(h), o, h->JY, h->W, st, k0, k1);
     } else {
         AsmOut<double> o{R, static_cast<double*>(vals), nullptr, h->status};
-        e = launch_assemble_fp64(kern, h->geom, h->qd, h->crk, fields_of<double>(h), o, h->JY, h->W, st);
+        e = launch_assemble_fp64(kern, h->geom, h->qd, h->crk, fields_of<double>(h), o, h->JY, h->W, st, k0, k1);
     }
     if (e != cudaSuccess) return cuda_fail(e, "assembly launch");
     return TPFA_OK;
@@ -550,19 +562,70 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
         cudaGetLastError();
         return fail(TPFA_ERR_OOM, "device allocation failed for the host-buffer entry point");
     }
-    cudaError_t e = cudaMemcpyAsync(h->h_p, p_host, pb, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "pressure upload");
+    cudaError_t e = cudaSuccess;
+    if (!h->h_up) {
+        e = cudaStreamCreateWithFlags(&h->h_up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->h_down, cudaStreamNonBlocking);
+        for (auto& ev : h->h_ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
+    }
+    // Pipeline over slabs of whole z-planes (a multiple of 8 planes, so of
+    // either block height): the upload of slab s+1's pressure, the assembly
+    // of slab s and the download of slab s-1's outputs overlap on three
+    // streams.  A slab reads the pressure of its planes and of the plane
+    // below its last one; planes are uploaded once, in order.
+    const int nz = h->nz;
+    int slab = ((nz + tpfa_grid::kMaxSlabs / 2 - 1) / (tpfa_grid::kMaxSlabs / 2) + 7) / 8 * 8;
+    if (slab < 8) slab = 8;
+    const int nslab = (nz + slab - 1) / slab;
+    const size_t plane = (size_t)h->nx * h->ny;
+    cudaEvent_t* ev_up = h->h_ev;
+    cudaEvent_t* ev_cmp = h->h_ev + tpfa_grid::kMaxSlabs;
+    cudaEvent_t ev_start = h->h_ev[2 * tpfa_grid::kMaxSlabs], ev_done = h->h_ev[2 * tpfa_grid::kMaxSlabs + 1];
+    e = cudaEventRecord(ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->h_up, ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->h_down, ev_start, 0);
     const void* saved = h->p;
     h->p = h->h_p;
-    rc = launch(h, AsmKernel::YMarch, h->h_R, h->h_vals, h->prec == TPFA_MIXED ? h->h_diag : nullptr, st);
+    int up_to = 0;
+    for (int s = 0; s < nslab && e == cudaSuccess && rc == TPFA_OK; ++s) {
+        const int k0 = s * slab, k1 = std::min(nz, k0 + slab);
+        const int need = std::min(nz, k1 + 1);
+        if (need > up_to) {
+            const size_t off = h->real_size * plane * (size_t)up_to;
+            e = cudaMemcpyAsync(static_cast<char*>(h->h_p) + off, static_cast<const char*>(p_host) + off,
+                                h->real_size * plane * (size_t)(need - up_to), cudaMemcpyHostToDevice, h->h_up);
+            up_to = need;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_up[s], h->h_up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_up[s], 0);
+        if (e != cudaSuccess) break;
+        rc = launch(h, AsmKernel::YMarch, h->h_R, h->h_vals, h->prec == TPFA_MIXED ? h->h_diag : nullptr, st, k0, k1);
+        if (rc) break;
+        e = cudaEventRecord(ev_cmp[s], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->h_down, ev_cmp[s], 0);
+        const size_t r0 = plane * (size_t)k0, rn = plane * (size_t)(k1 - k0);
+        const long long v0 = row_start(h->geom, 0, 0, k0), v1 = k1 == nz ? h->nnz : row_start(h->geom, 0, 0, k1);
+        if (e == cudaSuccess && R_host)
+            e = cudaMemcpyAsync(R_host + r0, h->h_R + r0, sizeof(double) * rn, cudaMemcpyDeviceToHost, h->h_down);
+        if (e == cudaSuccess && vals_host)
+            e = cudaMemcpyAsync(static_cast<char*>(vals_host) + h->real_size * (size_t)v0,
+                                static_cast<char*>(h->h_vals) + h->real_size * (size_t)v0,
+                                h->real_size * (size_t)(v1 - v0), cudaMemcpyDeviceToHost, h->h_down);
+        if (e == cudaSuccess && diag64_host && h->prec == TPFA_MIXED)
+            e = cudaMemcpyAsync(diag64_host + r0, h->h_diag + r0, sizeof(double) * rn, cudaMemcpyDeviceToHost,
+                                h->h_down);
+    }
     h->p = saved;
+    // whatever was enqueued completes before the call returns
+    cudaError_t e2 = cudaEventRecord(ev_done, h->h_down);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, ev_done, 0);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->h_up);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
     if (rc) return rc;
-    if (R_host) e = cudaMemcpyAsync(R_host, h->h_R, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(vals_host, h->h_vals, vb, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && diag64_host && h->prec == TPFA_MIXED)
-        e = cudaMemcpyAsync(diag64_host, h->h_diag, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "result download");
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return cuda_fail(e, "host-buffer pipeline");
     return TPFA_OK;
 }
 

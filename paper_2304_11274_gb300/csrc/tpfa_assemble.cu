@@ -79,9 +79,11 @@ static cudaError_t launch_naive_t(const GridGeom& g, const typename PhysOf<Real>
     return cudaGetLastError();
 }
 
+// Planes [k0, k1) of the grid (k0 a multiple of W); the whole grid by default.
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
 static cudaError_t launch_ymarch_w(const GridGeom& g, const typename PhysOf<Real>::type& q,
-                                   const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, cudaStream_t st) {
+                                   const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int k0, int k1,
+                                   cudaStream_t st) {
     constexpr int smem = ymarch_smem_bytes<Real, W>();
     static bool attr_set = false;  // per instantiation; the attribute is per function
     if (!attr_set) {
@@ -91,50 +93,52 @@ static cudaError_t launch_ymarch_w(const GridGeom& g, const typename PhysOf<Real
         attr_set = true;
     }
     dim3 block(32, W, 1);
-    dim3 grid((g.nx + 31) / 32, (g.ny + JY - 1) / JY, (g.nz + W - 1) / W);
-    k_assemble_ymarch<Real, DIAG, CRK, JAC, W><<<grid, block, smem, st>>>(g, q, f, o, JY);
+    dim3 grid((g.nx + 31) / 32, (g.ny + JY - 1) / JY, (k1 - k0 + W - 1) / W);
+    k_assemble_ymarch<Real, DIAG, CRK, JAC, W><<<grid, block, smem, st>>>(g, q, f, o, JY, k0 / W);
     return cudaGetLastError();
 }
 
 template <typename Real, bool DIAG, bool CRK, bool JAC>
 static cudaError_t launch_ymarch_t(const GridGeom& g, const typename PhysOf<Real>::type& q,
-                                   const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int W,
-                                   cudaStream_t st) {
-    if (W == 8) return launch_ymarch_w<Real, DIAG, CRK, JAC, 8>(g, q, f, o, JY, st);
-    return launch_ymarch_w<Real, DIAG, CRK, JAC, 4>(g, q, f, o, JY, st);
+                                   const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int W, int k0,
+                                   int k1, cudaStream_t st) {
+    if (W == 8) return launch_ymarch_w<Real, DIAG, CRK, JAC, 8>(g, q, f, o, JY, k0, k1, st);
+    return launch_ymarch_w<Real, DIAG, CRK, JAC, 4>(g, q, f, o, JY, k0, k1, st);
 }
 
 template <typename Real>
 static cudaError_t dispatch(AsmKernel kern, const GridGeom& g, const typename PhysOf<Real>::type& q,
-                            bool crk, const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int W,
-                            cudaStream_t st) {
+                            bool crk, const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int W, int k0,
+                            int k1, cudaStream_t st) {
     const bool jac = o.vals != nullptr;
+    if (k1 < 0 || k1 > g.nz) k1 = g.nz;
+    if (k0 < 0 || k0 % W != 0 || k0 >= k1) k0 = 0;  // only W-aligned plane ranges are split
     if (kern == AsmKernel::Naive) {
         if (crk) return jac ? launch_naive_t<Real, true, true>(g, q, f, o, st) : launch_naive_t<Real, true, false>(g, q, f, o, st);
         return jac ? launch_naive_t<Real, false, true>(g, q, f, o, st) : launch_naive_t<Real, false, false>(g, q, f, o, st);
     }
     if (g.diag) {
-        if (crk) return jac ? launch_ymarch_t<Real, true, true, true>(g, q, f, o, JY, W, st)
-                            : launch_ymarch_t<Real, true, true, false>(g, q, f, o, JY, W, st);
-        return jac ? launch_ymarch_t<Real, true, false, true>(g, q, f, o, JY, W, st)
-                   : launch_ymarch_t<Real, true, false, false>(g, q, f, o, JY, W, st);
+        if (crk) return jac ? launch_ymarch_t<Real, true, true, true>(g, q, f, o, JY, W, k0, k1, st)
+                            : launch_ymarch_t<Real, true, true, false>(g, q, f, o, JY, W, k0, k1, st);
+        return jac ? launch_ymarch_t<Real, true, false, true>(g, q, f, o, JY, W, k0, k1, st)
+                   : launch_ymarch_t<Real, true, false, false>(g, q, f, o, JY, W, k0, k1, st);
     }
-    if (crk) return jac ? launch_ymarch_t<Real, false, true, true>(g, q, f, o, JY, W, st)
-                        : launch_ymarch_t<Real, false, true, false>(g, q, f, o, JY, W, st);
-    return jac ? launch_ymarch_t<Real, false, false, true>(g, q, f, o, JY, W, st)
-               : launch_ymarch_t<Real, false, false, false>(g, q, f, o, JY, W, st);
+    if (crk) return jac ? launch_ymarch_t<Real, false, true, true>(g, q, f, o, JY, W, k0, k1, st)
+                        : launch_ymarch_t<Real, false, true, false>(g, q, f, o, JY, W, k0, k1, st);
+    return jac ? launch_ymarch_t<Real, false, false, true>(g, q, f, o, JY, W, k0, k1, st)
+               : launch_ymarch_t<Real, false, false, false>(g, q, f, o, JY, W, k0, k1, st);
 }
 
 cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk,
                                   const AsmFields<float>& f, const AsmOut<float>& o, int JY, int W,
-                                  cudaStream_t st) {
-    return dispatch<float>(kern, g, q, crk, f, o, JY, W, st);
+                                  cudaStream_t st, int k0, int k1) {
+    return dispatch<float>(kern, g, q, crk, f, o, JY, W, k0, k1, st);
 }
 
 cudaError_t launch_assemble_fp64(AsmKernel kern, const GridGeom& g, const PhysD& q, bool crk,
                                  const AsmFields<double>& f, const AsmOut<double>& o, int JY, int W,
-                                 cudaStream_t st) {
-    return dispatch<double>(kern, g, q, crk, f, o, JY, W, st);
+                                 cudaStream_t st, int k0, int k1) {
+    return dispatch<double>(kern, g, q, crk, f, o, JY, W, k0, k1, st);
 }
 
 }  // namespace tpfa

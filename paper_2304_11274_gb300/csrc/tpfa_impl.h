@@ -14,13 +14,15 @@ struct PhysD;
 
 enum class AsmKernel { Naive, YMarch };
 
-// JY: rows per warp march; W: warps (z-planes) per block, 4 or 8.
+// JY: rows per warp march; W: warps (z-planes) per block, 4 or 8.  The tiled
+// kernel may be restricted to the planes [k0, k1) (k0 a multiple of W; rows
+// outside are neither read as outputs nor written); the default is the grid.
 cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk,
                                   const AsmFields<float>& f, const AsmOut<float>& o, int JY, int W,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int k0 = 0, int k1 = -1);
 cudaError_t launch_assemble_fp64(AsmKernel kern, const GridGeom& g, const PhysD& q, bool crk,
                                  const AsmFields<double>& f, const AsmOut<double>& o, int JY, int W,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int k0 = 0, int k1 = -1);
 
 // Setup kernels (tpfa_setup.cu).
 struct SetupPhys {

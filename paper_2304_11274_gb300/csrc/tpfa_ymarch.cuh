@@ -596,9 +596,10 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
 
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
 __global__ void __launch_bounds__(32 * W, (sizeof(Real) == 4 ? 16 : 8) / W)
-    k_assemble_ymarch(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f, AsmOut<Real> o, int JY) {
+    k_assemble_ymarch(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f, AsmOut<Real> o, int JY,
+                      int bz0) {
     extern __shared__ __align__(16) unsigned char smem[];
-    ymarch_tile<Real, DIAG, CRK, JAC, W>(g, q, f, o, JY, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    ymarch_tile<Real, DIAG, CRK, JAC, W>(g, q, f, o, JY, blockIdx.x, blockIdx.y, bz0 + (int)blockIdx.z, smem);
 }
 
 }  // namespace tpfa
