@@ -92,7 +92,9 @@ typedef struct {
 /*
  * Create a grid (Section 3 problem statement; Section 6 layout).
  *   out        : receives the handle.
- *   nx, ny, nz : grid size, each >= 1, N = nx ny nz < 2^31 (else TOO_LARGE).
+ *   nx, ny, nz : grid size, each >= 1, N = nx ny nz < 2^31, and one z-plane's
+ *                Jacobian entries addressable in 32 bits, 11 nx ny < 2^31
+ *                (about 195 M cells per plane); else TPFA_ERR_TOO_LARGE.
  *   prm        : physical constants and connectivity (copied).
  *   prec       : TPFA_FP64 or TPFA_MIXED.
  *   perm_dev   : N doubles, permeability k (m^2, >= 0), read during the call only.

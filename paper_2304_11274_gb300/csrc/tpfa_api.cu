@@ -417,6 +417,10 @@ int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params
     if (nx < 1 || ny < 1 || nz < 1) return fail(TPFA_ERR_INVALID_ARG, "grid sizes must be >= 1 (%d %d %d)", nx, ny, nz);
     const long long N = (long long)nx * ny * nz;
     if (N >= (1LL << 31)) return fail(TPFA_ERR_TOO_LARGE, "N = %lld cells exceeds 2^31 - 1", N);
+    // the assembly kernels address one z-plane's CSR entries in 32 bits
+    if ((long long)nx * ny * 11 >= (1LL << 31))
+        return fail(TPFA_ERR_TOO_LARGE, "a %d x %d z-plane has too many Jacobian entries (limit 11 nx ny < 2^31)",
+                    nx, ny);
     int rc = check_params(prm);
     if (rc) return rc;
     if (prec != TPFA_FP64 && prec != TPFA_MIXED) return fail(TPFA_ERR_INVALID_ARG, "bad precision %d", (int)prec);

@@ -174,9 +174,13 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         s0 = s1;
         s1 = s2;
         s2 = st;
-        const bool full = M.xint && zint && j > 0 && j + 1 < M.ny;
-        U = full ? M.template row_jvp<true>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp)
-                 : M.template row_jvp<false>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp);
+        const bool injk = zint && j > 0 && j + 1 < M.ny;
+        if (injk && M.xint)
+            U = M.template row_jvp<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp);
+        else if (injk)
+            U = M.template row_jvp<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp);
+        else
+            U = M.template row_jvp<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp);
         Ty_prev = D.Ty;
         Tpp_prev = D.Tpp;
         Tmp_prev = D.Tmp;

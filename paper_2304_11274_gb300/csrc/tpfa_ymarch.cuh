@@ -19,9 +19,12 @@
 //     dPhi == 0 breaks that symmetry (each end takes the other cell as
 //     upstream), so a warp that meets one re-evaluates those links directly;
 //   * rows with all ten neighbours (the interior) take a path with fixed slot
-//     positions; boundary rows use per-slot validity masks;
+//     positions; rows of a segment at an x boundary (j and k interior) take a
+//     path whose masks and offsets differ only in the edge lanes; the other
+//     boundary rows use per-slot validity masks;
 //   * the warp's Jacobian rows form one contiguous CSR segment whose offset is
-//     a closed form of (i0, j, k); values are staged in shared memory at their
+//     a closed form of (i0, j, k) (the y-row part advanced incrementally along
+//     the march); values are staged in shared memory at their
 //     offsets and written with 16-byte stores;
 //   * every input of row j+2 is requested with cp.async into a per-warp
 //     shared-memory ring at the start of step j, so loads are in flight a
@@ -104,7 +107,9 @@ struct YMarch {
     const AsmOut<Real>& o;
     int lane, i0, i, k, nx, ny, nxy, kb, ih;
     bool act, hact, zm, zp, xint, v16;
-    long long base_k, rowA, rowB;
+    long long base_k;
+    int rowA, rowB;  // CSR entries per y-row of plane k: rowA + (y links of the row) rowB
+    int X2;          // offset of this segment within a y-row whose j and k are interior
     int Sx0, ez;
 
     __device__ __forceinline__ YMarch(const GridGeom& g_, const Phys& q_, const AsmFields<Real>& f_,
@@ -125,9 +130,39 @@ struct YMarch {
         const long long plane = (long long)nx * ny + Ex * ny + (long long)nx * Ey + D * Ex * Ey;
         ez = axis_links(k, g.nz);
         base_k = (long long)k * plane + (long long)nxy * axis_links_before(k, g.nz);
-        rowA = nx + Ex + (long long)nx * ez;
-        rowB = nx + D * Ex;
+        rowA = (int)(nx + Ex + (long long)nx * ez);
+        rowB = (int)(nx + D * Ex);
         Sx0 = (int)axis_links_before(i0, nx);
+        X2 = i0 * (3 + ez) + Sx0 * (int)(1 + 2 * D);
+    }
+
+    // CSR offset of row (0, j, k) relative to the plane's first row (one
+    // plane's rows number fewer than 2^31: the grid has fewer than 2^31 / 11
+    // cells per plane whenever its pattern is addressable).
+    __device__ __forceinline__ int row_base(int j) const {
+        return j * rowA + (int)axis_links_before(j, ny) * rowB;
+    }
+    __device__ __forceinline__ int row_base_step(int j) const { return rowA + axis_links(j, ny) * rowB; }
+
+    // Row kinds: 2 = every neighbour exists (interior x-segment, j and k
+    // interior); 1 = j and k interior in a segment that touches an x boundary
+    // (the lanes at i = 0 and i = nx - 1 lack their -x or +x links); 0 = any
+    // other row.
+    static constexpr unsigned kFullMask = DIAG ? 0x7ffu : 0x575u;
+    static constexpr unsigned kXMinus = 0x92u;   // slots 1, 4, 7
+    static constexpr unsigned kXPlus = 0x248u;   // slots 3, 6, 9
+    template <int PATH>
+    __device__ __forceinline__ unsigned row_mask(int j) const {
+        if constexpr (PATH == 2) {
+            return kFullMask;
+        } else if constexpr (PATH == 1) {
+            unsigned m = kFullMask;
+            if (i == 0) m &= ~kXMinus;
+            if (i == nx - 1) m &= ~kXPlus;
+            return m;
+        } else {
+            return slot_mask(g, i, j, k);
+        }
     }
 
     // ---- row inputs, prefetched into a per-warp shared-memory ring of RING
@@ -351,22 +386,25 @@ struct YMarch {
     // Assemble row j.  P, C, N: rows j-1, j, j+1.  Uprev: links from row j-1
     // into row j.  buf: this step's staging buffer.  Returns the links from
     // row j into row j+1.
-    template <bool FULL>
+    template <int PATH>
     __device__ __forceinline__ YUp<Real> row(int j, const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
                                              const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev, Real Tpp_prev,
-                                             Real Tmp_prev, Real* buf) const {
-        const int ey = FULL ? 2 : axis_links(j, ny);
-        const unsigned mask = FULL ? (DIAG ? 0x7ffu : 0x575u) : slot_mask(g, i, j, k);
+                                             Real Tmp_prev, Real* buf, int rowbase) const {
+        constexpr bool FULL = PATH == 2, INJK = PATH >= 1;
+        constexpr int L = DIAG ? 11 : 7, LX = DIAG ? 3 : 1;  // interior row length; x links per side
+        const int ey = INJK ? 2 : axis_links(j, ny);
+        const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
         eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
 
         // offsets of this row's CSR segment and of this lane's row in it
         const int per = 1 + ey + ez, perx = 1 + g.diag * ey;
-        const int lane_off = FULL ? lane * (DIAG ? 11 : 7)
-                                  : (i - i0) * per + (int)(axis_links_before(i, nx) - Sx0) * perx;
-        const long long seg = base_k + (long long)j * rowA + axis_links_before(j, ny) * rowB +
-                              (long long)i0 * per + (long long)Sx0 * perx;
+        int lane_off;
+        if constexpr (FULL) lane_off = lane * L;
+        else if constexpr (INJK) lane_off = lane * L - ((i0 == 0 && lane > 0) ? LX : 0);
+        else lane_off = (i - i0) * per + (int)(axis_links_before(i, nx) - Sx0) * perx;
+        const long long seg = base_k + (rowbase + (INJK ? X2 : i0 * per + Sx0 * perx));
         const int aoff = JAC ? (int)(seg & (VEC - 1)) : 0;
 
         const RowSums out = sum_row(S, mask, C.c, D, buf + aoff + lane_off);
@@ -378,7 +416,10 @@ struct YMarch {
         }
         if (JAC) {
             const int iend = min(i0 + 32, nx);
-            const int seg_len = (iend - i0) * per + (int)(axis_links_before(iend, nx) - Sx0) * perx;
+            int seg_len;
+            if constexpr (FULL) seg_len = 32 * L;
+            else if constexpr (INJK) seg_len = (iend - i0) * L - (i0 == 0 ? LX : 0) - (iend == nx ? LX : 0);
+            else seg_len = (iend - i0) * per + (int)(axis_links_before(iend, nx) - Sx0) * perx;
             write_segment(buf, seg, aoff, seg_len);
         }
         return U;
@@ -388,12 +429,12 @@ struct YMarch {
     // j, j+1; wzm, wzp the vertical neighbours'.  Per link the term
     // dF/dp_K w_K + dF/dp_L w_L is one FP32 fma; the terms and the residual's
     // fluxes share one FP32x2 Kahan sum in slot order, then dA/dp w_K.
-    template <bool FULL>
+    template <int PATH>
     __device__ __forceinline__ YUp<Real> row_jvp(int j, const YRow<Real>& P, const YRow<Real>& C,
                                                  const YRow<Real>& N, const YIn<Real>& D, const YUp<Real>& Uprev,
                                                  Real Ty_prev, Real Tpp_prev, Real Tmp_prev, const YW& wP,
                                                  const YW& wC, const YW& wN, float wzm, float wzp) const {
-        const unsigned mask = FULL ? (DIAG ? 0x7ffu : 0x575u) : slot_mask(g, i, j, k);
+        const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
         eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
@@ -568,6 +609,7 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
     }
     YUp<Real> U = M.up_links(P, C, Ty_prev, Tpp_prev, Tmp_prev);
     int s0 = 1, s1 = 2, s2 = 0;  // ring slots of rows j, j+1, j+2
+    int rowbase = M.row_base(j0);
 
     for (int j = j0; j < j1; ++j) {
         // row j+2 is requested now and used two steps later; row j+1 arrived
@@ -581,9 +623,11 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
         s2 = st;
         Real* buf = stage + ((j - j0) & 1) * BUF;
         M.buffer_ready();
-        const bool full = M.xint && zint && j > 0 && j + 1 < M.ny;
-        U = full ? M.template row<true>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf)
-                 : M.template row<false>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf);
+        const bool injk = zint && j > 0 && j + 1 < M.ny;
+        if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf, rowbase);
+        else if (injk) U = M.template row<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf, rowbase);
+        else U = M.template row<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf, rowbase);
+        rowbase += M.row_base_step(j);
         Ty_prev = D.Ty;
         Tpp_prev = D.Tpp;
         Tmp_prev = D.Tmp;

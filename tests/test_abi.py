@@ -71,6 +71,9 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.tpfa_create_grid(ctypes.byref(h), 0, 4, 4, ctypes.byref(prm), 0, dummy, dummy, dummy, None) == -1
     assert b"grid sizes" in lib.tpfa_last_error_string()
     assert lib.tpfa_create_grid(ctypes.byref(h), 2048, 2048, 1024, ctypes.byref(prm), 0, dummy, dummy, dummy, None) == -4
+    # fewer than 2^31 cells, but one z-plane's 11 nx ny Jacobian entries exceed 32-bit offsets
+    assert lib.tpfa_create_grid(ctypes.byref(h), 14000, 14000, 1, ctypes.byref(prm), 0, dummy, dummy, dummy, None) == -4
+    assert b"z-plane" in lib.tpfa_last_error_string()
     bad = _capi.TPFAParams(1000.0, 1e7, 4.5e-10, 1e-3, 9.81, 86400.0, 0.0, 10.0, 10.0, 2.0, 8)
     assert lib.tpfa_create_grid(ctypes.byref(h), 4, 4, 4, ctypes.byref(bad), 0, dummy, dummy, dummy, None) == -1
     assert b"connectivity" in lib.tpfa_last_error_string()
@@ -79,6 +82,24 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.tpfa_create_grid(ctypes.byref(h), 4, 4, 4, ctypes.byref(prm), 7, dummy, dummy, dummy, None) == -1
     assert lib.tpfa_create_grid(ctypes.byref(h), 4, 4, 4, ctypes.byref(prm), 0, None, dummy, dummy, None) == -1
     assert lib.tpfa_nnz(4, 4, 4, 7) == -1
+
+
+def test_mesh_arguments_rejected_before_any_device_work(lib):
+    prm = _capi.TPFAParams(1000.0, 1e7, 4.5e-10, 1e-3, 9.81, 86400.0, 0.0, 10.0, 10.0, 2.0, 6)
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    assert lib.tpfa_create_mesh(None, 4, 0, ctypes.byref(prm), 0, None, None, None, dummy, dummy, dummy, None) == -1
+    assert lib.tpfa_create_mesh(ctypes.byref(h), 0, 0, ctypes.byref(prm), 0, None, None, None, dummy, dummy, dummy,
+                                None) == -1
+    assert lib.tpfa_create_mesh(ctypes.byref(h), 1 << 31, 0, ctypes.byref(prm), 0, None, None, None, dummy, dummy,
+                                dummy, None) == -4
+    assert lib.tpfa_create_mesh(ctypes.byref(h), 4, 3, ctypes.byref(prm), 0, None, None, None, dummy, dummy, dummy,
+                                None) == -1
+    assert b"non-NULL" in lib.tpfa_last_error_string()
+    assert lib.tpfa_destroy_mesh(None) == 0
+    assert lib.tpfa_mesh_assemble(None, None, None, None, None) == -1
+    assert lib.tpfa_mesh_set_state(None, None, None, None) == -1
+    assert lib.tpfa_mesh_sync_status(None, None) == -1
 
 
 def test_null_handle_calls(lib):
