@@ -533,9 +533,17 @@ def measure_adjoint(dev, stream, reps=20):
     torch.cuda.synchronize(dev)
     g.sync_status()
     ms = a.elapsed_time(b) / reps
+    tiling = g.tiling()
     g.close()
+    # reads p, p^n, depth, k (4 B each), 5 owned T (20 B), m^n and v (8 B each); writes g_p, g_lnk
+    nbytes = prob.n * (4 * 4 + 5 * 4 + 8 + 8 + 16)
+    peak, _ = measured_peaks()
     return {"grid": [prob.nx, prob.ny, prob.nz], "value": prob.n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
-            "outputs": "g_p and g_lnk (FP64)", "bound": "fp64 pipe (v-weighted sums in FP64)"}
+            "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": nbytes},
+            "kernel": "k_vjp_ymarch<DIAG,!CR,W=%d>" % tiling[1],
+            "tiling": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]},
+            "outputs": "g_p and g_lnk (FP64)"}
 
 
 # ---------------------------------------------------------------------- oracle on the host

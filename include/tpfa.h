@@ -169,9 +169,17 @@ int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream);
  * harmonic transmissibilities, d Upsilon_KL/d ln k_K = Upsilon_KL k_L/(k_K + k_L).
  * Densities, upwind choices and mobilities are recomputed, nothing is stored
  * by the forward pass.  v_dev, g_p_dev: N doubles; g_lnk_dev: N doubles or
- * NULL.  Links in the path's precision, sums and outputs in FP64.
+ * NULL.  TPFA_FP64: links, sums and outputs in FP64.  TPFA_MIXED: FP32 links;
+ * each link's term is an FP32 product with v_K - v_L (formed in FP64), the
+ * terms are compensated FP32 sums combined in FP64, the outputs FP64.
  */
 int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_dev, void* stream);
+
+/* As tpfa_vjp with an explicit kernel variant (TPFA_MIXED: the tiled march
+ * and the naive gather give identical bits; TPFA_FP64 has one kernel and
+ * ignores the choice). */
+int tpfa_vjp_kernel(tpfa_handle h, tpfa_kernel kern, const double* v_dev, double* g_p_dev, double* g_lnk_dev,
+                    void* stream);
 
 /*
  * Matrix-free Jacobian-vector product at the bound state (the operator a
@@ -239,7 +247,10 @@ int tpfa_sync_status(tpfa_handle h, void* stream);
  * Tiling of the assembly kernel: a warp marches along y over
  * `rows_per_march` rows of a 32-cell x-segment, and a block stacks
  * `warps_per_block` (4 or 8) consecutive z-planes.  Results do not depend on
- * the tiling (every row is summed in the same order); only speed does.
+ * the tiling (every row is summed in the same order); only speed does.  The
+ * J w and adjoint marches use the same tiling, with the rows per march
+ * halved (down to 8) while the launch has fewer than four blocks per
+ * multiprocessor.
  */
 int tpfa_set_tiling(tpfa_handle h, int rows_per_march, int warps_per_block);
 int tpfa_get_tiling(tpfa_handle h, int* rows_per_march, int* warps_per_block);

@@ -76,6 +76,7 @@ SIGNATURES = [
     ("tpfa_assemble_jacobian_host", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("tpfa_set_permeability", _I, [_VP, _VP, _VP]),
     ("tpfa_vjp", _I, [_VP, _VP, _VP, _VP, _VP]),
+    ("tpfa_vjp_kernel", _I, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     ("tpfa_jvp", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_jvp_kernel", _I, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     ("tpfa_linear_solve", _I, [_VP, _VP, _VP, ctypes.POINTER(TPFAKrylovOpts), ctypes.POINTER(TPFAKrylovStats), _VP]),

@@ -159,12 +159,13 @@ class Grid:
         check(self.lib.tpfa_set_permeability(self.handle, _ptr(k), _stream(stream)))
         self._perm = k  # read asynchronously: keep it alive
 
-    def vjp(self, v, want_lnk=True, stream=None):
+    def vjp(self, v, want_lnk=True, kernel="auto", stream=None):
         """(g_p, g_lnk) = (v^T dR/dp, v^T dR/d ln k) at the bound state, FP64."""
         v = _dev_f64(v, self.device)
         g_p = torch.empty(self.n, dtype=torch.float64, device=self.device)
         g_lnk = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_lnk else None
-        check(self.lib.tpfa_vjp(self.handle, _ptr(v), _ptr(g_p), _ptr(g_lnk), _stream(stream)))
+        check(self.lib.tpfa_vjp_kernel(self.handle, _capi.KERNELS[kernel], _ptr(v), _ptr(g_p), _ptr(g_lnk),
+                                       _stream(stream)))
         self._v = v
         return g_p, g_lnk
 

@@ -91,6 +91,7 @@ struct tpfa_grid {
     void* T[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // Tx, Ty, Tz, Tpp, Tmp
     void* z = nullptr;
     void* kperm = nullptr;  // permeability in the field type (adjoint)
+    LinkGeo lg{};           // distance / area per link direction (adjoint)
     double* phi0_d = nullptr;
     void* phi0_r = nullptr;  // phi0 in the field type (mixed path with c_r != 0)
     double* mn = nullptr;
@@ -102,6 +103,7 @@ struct tpfa_grid {
     const void* pn = nullptr;
     bool has_state = false;
     int JY = 32;  // rows per warp march (tpfa_autotune may change it)
+    int sms = 0;  // multiprocessors of the grid's device
     int W = 4;    // warps (z-planes) per block
     // buffers of the host-memory entry point, allocated on first use
     void* h_p = nullptr;
@@ -207,6 +209,16 @@ int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, 
 int check_handle(tpfa_handle h) {
     if (!h) return fail(TPFA_ERR_INVALID_ARG, "handle is NULL");
     return TPFA_OK;
+}
+
+// Rows per march for the J w and adjoint marches: the grid's tiling, halved
+// (down to 8) until the launch has at least four blocks per multiprocessor,
+// so that small grids still fill the GPU.
+int march_rows(const tpfa_grid* h) {
+    int jy = h->JY;
+    const long long bx = (h->nx + 31) / 32, bz = (h->nz + h->W - 1) / h->W;
+    while (jy > 8 && h->sms > 0 && bx * ((h->ny + jy - 1) / jy) * bz < 4LL * h->sms) jy /= 2;
+    return jy;
 }
 
 // Newton / Krylov workspace: the assembled Jacobian, R, ten FP64 vectors,
@@ -432,6 +444,10 @@ int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params
 
     tpfa_grid* h = new tpfa_grid();
     h->device = dev;
+    if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        h->sms = 0;
+    }
     h->nx = nx, h->ny = ny, h->nz = nz, h->N = N;
     h->prec = prec;
     h->prm = *prm;
@@ -443,6 +459,9 @@ int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params
     h->qf = PhysF{(float)prm->rho_ref, (float)prm->p_ref, (float)prm->c_f, (float)(1.0 / prm->mu),
                   (float)prm->g, (float)(0.5 * prm->g), (float)V_dt, (float)prm->c_r};
     h->sp = SetupPhys{prm->dx, prm->dy, prm->dz, prm->rho_ref, prm->p_ref, prm->c_f, prm->c_r, V_dt};
+    h->lg = LinkGeo{(float)(prm->dx / (prm->dy * prm->dz)), (float)(prm->dy / (prm->dx * prm->dz)),
+                    (float)(prm->dz / (prm->dx * prm->dy)),
+                    (float)((prm->dx * prm->dx + prm->dy * prm->dy) / (prm->dz * prm->dx * prm->dy))};
     h->nnz = total_nnz(h->geom);
 
     const size_t rb = h->real_size * (size_t)N;
@@ -653,22 +672,34 @@ int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream) {
     return TPFA_OK;
 }
 
-int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_dev, void* stream) {
+int tpfa_vjp_kernel(tpfa_handle h, tpfa_kernel kern, const double* v_dev, double* g_p_dev, double* g_lnk_dev,
+                    void* stream) {
     int rc = check_handle(h);
     if (rc) return rc;
     if (!v_dev || !g_p_dev) return fail(TPFA_ERR_INVALID_ARG, "v and g_p must be non-NULL");
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    AsmKernel k;
+    switch (kern) {
+        case TPFA_KERNEL_AUTO:
+        case TPFA_KERNEL_TILED: k = AsmKernel::YMarch; break;
+        case TPFA_KERNEL_NAIVE: k = AsmKernel::Naive; break;
+        default: return fail(TPFA_ERR_INVALID_ARG, "bad kernel variant %d", (int)kern);
+    }
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (h->prec == TPFA_MIXED)
-        e = launch_vjp_mixed(h->geom, h->qf, h->crk, fields_of<float>(h), (const float*)h->kperm, v_dev, g_p_dev,
-                             g_lnk_dev, h->status, st);
+        e = launch_vjp_mixed(k, h->geom, h->qf, h->crk, fields_of<float>(h), (const float*)h->kperm, h->lg, v_dev,
+                             g_p_dev, g_lnk_dev, h->status, march_rows(h), h->W, st);
     else
         e = launch_vjp_fp64(h->geom, h->qd, h->crk, fields_of<double>(h), (const double*)h->kperm, v_dev, g_p_dev,
                             g_lnk_dev, h->status, st);
     if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
     return TPFA_OK;
+}
+
+int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_dev, void* stream) {
+    return tpfa_vjp_kernel(h, TPFA_KERNEL_AUTO, v_dev, g_p_dev, g_lnk_dev, stream);
 }
 
 int tpfa_jvp_kernel(tpfa_handle h, tpfa_kernel kern, const double* w_dev, double* Jw_dev, double* R_dev,
@@ -688,8 +719,8 @@ int tpfa_jvp_kernel(tpfa_handle h, tpfa_kernel kern, const double* w_dev, double
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (h->prec == TPFA_MIXED)
-        e = launch_jvp_mixed(k, h->geom, h->qf, h->crk, fields_of<float>(h), w_dev, Jw_dev, R_dev, h->status, h->JY,
-                             h->W, st);
+        e = launch_jvp_mixed(k, h->geom, h->qf, h->crk, fields_of<float>(h), w_dev, Jw_dev, R_dev, h->status,
+                             march_rows(h), h->W, st);
     else
         e = launch_jvp_fp64(h->geom, h->qd, h->crk, fields_of<double>(h), w_dev, Jw_dev, R_dev, h->status, st);
     if (e != cudaSuccess) return cuda_fail(e, "jvp launch");

@@ -83,6 +83,33 @@ __device__ __forceinline__ float narrow_rz(double x) {
     return (float)x;
 }
 
+// A double as an unevaluated FP32 pair v = hi + lo (hi the truncation of v,
+// lo the exact remainder narrowed; |lo| < ulp(hi)), so differences of nearby
+// values can be formed in FP32: (hi_a - hi_b) + (lo_a - lo_b) is accurate to
+// a few float ulps of a - b itself (hi_a - hi_b is exact when a and b are
+// within a factor of two).
+struct F2Split {
+    float hi, lo;
+};
+__device__ __forceinline__ F2Split split_f2(double v) {
+    F2Split r;
+    r.hi = narrow_rz(v);
+    r.lo = narrow_rz(__dadd_rn(v, -widen(r.hi)));
+    return r;
+}
+
+// a - b for two split doubles, in FP32.
+__device__ __forceinline__ float diff_f2(const F2Split& a, const F2Split& b) {
+    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
+
+// Distance over area of each link direction, the geometric factor of the
+// two-point transmissibility (x faces, y faces, z faces, in-plane diagonals).
+struct LinkGeo {
+    float cx, cy, cz, cd;
+};
+
+
 // ---------------------------------------------------------------- Kahan
 
 struct Kahan32 {

@@ -45,9 +45,12 @@ cudaError_t launch_prev_mass_f32(const SetupPhys& s, const float* pn, const doub
 cudaError_t launch_prev_mass_f64(const SetupPhys& s, const double* pn, const double* phi0, double* mn,
                                  long long n, cudaStream_t st);
 // Adjoint (tpfa_vjp.cu).
-cudaError_t launch_vjp_mixed(const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
-                             const float* kperm, const double* v, double* g_p, double* g_lnk,
-                             unsigned int* status, cudaStream_t st);
+struct LinkGeo;
+// The mixed path's adjoint runs the y-march (JY rows per march, W warps per
+// block) or its naive gather twin; lg: distance over area per link direction.
+cudaError_t launch_vjp_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
+                             const float* kperm, const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
+                             unsigned int* status, int JY, int W, cudaStream_t st);
 cudaError_t launch_vjp_fp64(const GridGeom& g, const PhysD& q, bool crk, const AsmFields<double>& f,
                             const double* kperm, const double* v, double* g_p, double* g_lnk,
                             unsigned int* status, cudaStream_t st);

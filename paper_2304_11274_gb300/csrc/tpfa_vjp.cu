@@ -14,12 +14,26 @@
 // the forward assembly and this pass: densities, upwind choices and
 // mobilities are recomputed (gather form, one thread per cell, no atomics).
 //
-// Arithmetic: links in the path's precision (FP32 on the mixed path), the
-// v-weighted sums and both outputs in FP64.
+// FP64 path: links, sums and outputs in FP64, one thread per cell.
+//
+// Mixed path: with dF_Li/dp_i = -dF_iL/dp_i except at an exact tie, and
+// k_L / (k_i + k_L) = Upsilon_iL (d/A)_iL / (2 k_i) for the harmonic
+// two-point transmissibility,
+//   g_p[i]   = v_i dA_i/dp_i + sum_L dF_iL/dp_i (v_i - v_L) + sum_L v_L delta_iL
+//   g_lnk[i] = sum_L F_iL Upsilon_iL (d/A)_iL / (2 k_i) (v_i - v_L)
+// where delta_iL = dF_iL/dp_i + dF_Li/dp_i vanishes except at a tie.  Each v
+// is split into an FP32 pair hi + lo, and v_i - v_L = (hi_i - hi_L) + (lo_i -
+// lo_L) is formed in FP32 (for the two vertical links: in FP64, then
+// narrowed), so each term is accurate relative to itself (a smooth v loses
+// nothing); the terms are FP32 products Kahan-summed in FP32 in slot order
+// and combined in FP64.  Two
+// kernels give identical bits: the y-march of the assembly (its adjoint
+// mode, the production kernel) and a one-thread-per-cell gather with
+// checked loads.
 #include <cuda_runtime.h>
 
 #include "tpfa_impl.h"
-#include "tpfa_row.cuh"
+#include "tpfa_ymarch.cuh"
 
 namespace tpfa {
 
@@ -113,6 +127,193 @@ __global__ void __launch_bounds__(256) k_vjp(GridGeom g, typename PhysOf<Real>::
     if (nonfinite(gp) || nonfinite(glnk)) atomicOr(status, STATUS_NONFINITE);
 }
 
+__device__ __forceinline__ float geo_of(const LinkGeo& lg, int s) {
+    switch (s) {
+        case 0:
+        case 10: return lg.cz;
+        case 2:
+        case 8: return lg.cy;
+        case 4:
+        case 6: return lg.cx;
+        default: return lg.cd;
+    }
+}
+
+// The mixed path's adjoint, one thread per cell (the march's twin).
+template <bool CRK>
+__global__ void __launch_bounds__(256) k_vjp_mixed(GridGeom g, PhysF q, AsmFields<float> f,
+                                                   const float* __restrict__ kperm, LinkGeo lg,
+                                                   const double* __restrict__ v, double* __restrict__ g_p,
+                                                   double* __restrict__ g_lnk, unsigned int* status) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int nx = g.nx, nxy = nx * g.ny;
+    const int c = i + nx * j + nxy * k;
+    const long long NN = (long long)nxy * g.nz;
+    const unsigned mask = slot_mask(g, i, j, k);
+    const int off[NSLOT] = {-nxy, -nx - 1, -nx, -nx + 1, -1, 0, 1, nx - 1, nx, nx + 1, nxy};
+    const CellVal<float> me = make_cell(q, ld_chk(f.p, c, NN, status), ld_chk(f.z, c, NN, status));
+    const double vi = ld_chk(v, c, NN, status);
+    const F2Split si = split_f2(vi);
+    const float ki = ld_chk(kperm, c, NN, status);
+    const float inv2k = ki > 0.f ? __fdiv_rn(0.5f, ki) : 0.f;
+    Kahan32 kp, kk;
+    double corr = 0.0;
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        if (s == SLOT_SELF || !(mask & (1u << s))) continue;
+        const int d = c + off[s];
+        const float* Tp;
+        int ti;
+        switch (s) {
+            case 0: Tp = f.Tz; ti = d; break;
+            case 1: Tp = f.Tpp; ti = d; break;
+            case 2: Tp = f.Ty; ti = d; break;
+            case 3: Tp = f.Tmp; ti = d; break;
+            case 4: Tp = f.Tx; ti = d; break;
+            case 6: Tp = f.Tx; ti = c; break;
+            case 7: Tp = f.Tmp; ti = c; break;
+            case 8: Tp = f.Ty; ti = c; break;
+            case 9: Tp = f.Tpp; ti = c; break;
+            default: Tp = f.Tz; ti = c; break;
+        }
+        const float T = ld_chk(Tp, ti, NN, status);
+        const CellVal<float> nb = make_cell(q, ld_chk(f.p, d, NN, status), ld_chk(f.z, d, NN, status));
+        const LinkOut<float> L = link(q, T, me, nb);
+        const double vl = ld_chk(v, d, NN, status);
+        const bool vertical = s == 0 || s == 10;
+        const F2Split sl = split_f2(vl);
+        const float dv = vertical ? narrow_rz(__dadd_rn(vi, -vl)) : diff_f2(si, sl);
+        const float ratio = __fmul_rn(__fmul_rn(T, geo_of(lg, s)), inv2k);
+        kp.add(__fmul_rn(L.Da, dv));
+        kk.add(__fmul_rn(__fmul_rn(L.F, ratio), dv));
+        const float dLK = link(q, T, nb, me).Db;
+        const double vL = vertical ? vl : __dadd_rn(widen(sl.hi), widen(sl.lo));
+        corr = __fma_rn(vL, widen(__fadd_rn(L.Da, dLK)), corr);
+    }
+    const AccF acc = accumulation<CRK>(q, me.p, ld_chk(f.pn, c, NN, status), ld_chk(f.mn, c, NN, status), me.rho,
+                                       CRK ? ld_chk(f.phi0, c, NN, status) : 0.f);
+    const double gp = __dadd_rn(__fma_rn(vi, widen(acc.dA), __dadd_rn(widen(kp.s), -widen(kp.c))), corr);
+    const double gk = __dadd_rn(widen(kk.s), -widen(kk.c));
+    g_p[c] = gp;
+    if (g_lnk) g_lnk[c] = gk;
+    if (nonfinite(gp) || nonfinite(gk)) atomicOr(status, STATUS_NONFINITE);
+}
+
+// ---------------------------------------------------------------- y-march adjoint (mixed)
+
+template <int W>
+constexpr int vjp_smem_bytes() {
+    using M = YMarch<float, true, false, false, W, false, true>;
+    return W * (M::RING * M::NF * 32 * 4 + M::RING * 32 * 8 + M::RING * M::NW * 32 * 8);
+}
+
+template <bool DIAG, bool CRK, int W>
+__global__ void __launch_bounds__(32 * W, 16 / W)
+    k_vjp_ymarch(GridGeom g, PhysF q, AsmFields<float> f, AsmOut<float> o, const float* __restrict__ kperm,
+                 LinkGeo lg, const double* __restrict__ v, double* __restrict__ g_p, double* __restrict__ g_lnk,
+                 int JY) {
+    using M_t = YMarch<float, DIAG, CRK, false, W, false, true>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x, wi = threadIdx.y;
+    const int k = blockIdx.z * W + wi;
+    if (k >= g.nz) return;  // warp-uniform
+    float* ring = reinterpret_cast<float*>(smem) + wi * M_t::RING * M_t::NF * 32;
+    double* ringm = reinterpret_cast<double*>(reinterpret_cast<float*>(smem) + W * M_t::RING * M_t::NF * 32) +
+                    wi * M_t::RING * 32;
+    double* ringw = reinterpret_cast<double*>(reinterpret_cast<float*>(smem) + W * M_t::RING * M_t::NF * 32) +
+                    W * M_t::RING * 32 + wi * M_t::RING * M_t::NW * 32;
+    M_t M(g, q, f, o, lane, blockIdx.x * 32, k);
+    M.ring = ring;
+    M.ringm = ringm;
+    M.ringw = ringw;
+    M.wv = v;
+    M.kperm = kperm;
+    M.lg = lg;
+    M.gP = g_p;
+    M.gK = g_lnk;
+    const int j0 = blockIdx.y * JY;
+    const int j1 = min(j0 + JY, g.ny);
+    const bool zint = M.zm && M.zp;
+
+    M.issue_row(j0 - 1, 0);
+    M.issue_row(j0, 1);
+    M.issue_row(j0 + 1, 2);
+    M.wait_all_but_newest();
+    YRow<float> P = M.row_cells(0);
+    YRow<float> C = M.row_cells(1);
+    YV vP = M.v_row(0);
+    YV vC = M.v_row(1);
+    float Ty_prev, Tpp_prev, Tmp_prev;
+    {
+        const YIn<float> Dp = M.read_in(0);
+        Ty_prev = Dp.Ty;
+        Tpp_prev = Dp.Tpp;
+        Tmp_prev = Dp.Tmp;
+    }
+    YUp<float> U = M.up_links(P, C, Ty_prev, Tpp_prev, Tmp_prev);
+    int s0 = 1, s1 = 2, s2 = 0;  // ring slots of rows j, j+1, j+2
+
+    for (int j = j0; j < j1; ++j) {
+        M.issue_row(j + 2, s2);
+        M.wait_all_but_newest();
+        const YRow<float> N = M.row_cells(s1);
+        const YV vN = M.v_row(s1);
+        const YIn<float> D = M.read_in(s0);
+        const double* Wz = ringw + s0 * (M_t::NW * 32) + lane;
+        const double vd = Wz[0], vzm = Wz[64], vzp = Wz[96];
+        const float kC = ring[s0 * (M_t::NF * 32) + M_t::F_K * 32 + lane];
+        const int st = s0;
+        s0 = s1;
+        s1 = s2;
+        s2 = st;
+        const bool injk = zint && j > 0 && j + 1 < M.ny;
+        if (injk && M.xint)
+            U = M.template row_vjp<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC);
+        else if (injk)
+            U = M.template row_vjp<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC);
+        else
+            U = M.template row_vjp<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC);
+        Ty_prev = D.Ty;
+        Tpp_prev = D.Tpp;
+        Tmp_prev = D.Tmp;
+        P = C;
+        C = N;
+        vP = vC;
+        vC = vN;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <bool DIAG, bool CRK, int W>
+cudaError_t launch_vjp_ymarch_w(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const float* kperm,
+                                const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
+                                unsigned int* status, int JY, cudaStream_t st) {
+    constexpr int smem = vjp_smem_bytes<W>();
+    static bool attr = false;  // per-process: the attribute is set once per kernel instance
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_vjp_ymarch<DIAG, CRK, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 block(32, W, 1);
+    dim3 grid((g.nx + 31) / 32, (g.ny + JY - 1) / JY, (g.nz + W - 1) / W);
+    AsmOut<float> o{nullptr, nullptr, nullptr, status};
+    k_vjp_ymarch<DIAG, CRK, W><<<grid, block, smem, st>>>(g, q, f, o, kperm, lg, v, g_p, g_lnk, JY);
+    return cudaGetLastError();
+}
+
+template <bool DIAG, bool CRK>
+cudaError_t launch_vjp_ymarch_t(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const float* kperm,
+                                const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
+                                unsigned int* status, int JY, int W, cudaStream_t st) {
+    if (W == 8) return launch_vjp_ymarch_w<DIAG, CRK, 8>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
+    return launch_vjp_ymarch_w<DIAG, CRK, 4>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
+}
+
 // k stored in the path's precision for the adjoint.
 template <typename Real>
 __global__ void k_store_perm(const double* __restrict__ perm, Real* out, long long n) {
@@ -133,10 +334,22 @@ static cudaError_t launch_vjp_t(const GridGeom& g, const typename PhysOf<Real>::
     return cudaGetLastError();
 }
 
-cudaError_t launch_vjp_mixed(const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
-                             const float* kperm, const double* v, double* g_p, double* g_lnk,
-                             unsigned int* status, cudaStream_t st) {
-    return launch_vjp_t<float>(g, q, crk, f, kperm, v, g_p, g_lnk, status, st);
+cudaError_t launch_vjp_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
+                             const float* kperm, const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
+                             unsigned int* status, int JY, int W, cudaStream_t st) {
+    if (kern == AsmKernel::Naive) {
+        dim3 block(32, 8, 1);
+        dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+        if (crk) k_vjp_mixed<true><<<grid, block, 0, st>>>(g, q, f, kperm, lg, v, g_p, g_lnk, status);
+        else k_vjp_mixed<false><<<grid, block, 0, st>>>(g, q, f, kperm, lg, v, g_p, g_lnk, status);
+        return cudaGetLastError();
+    }
+    if (g.diag) {
+        return crk ? launch_vjp_ymarch_t<true, true>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st)
+                   : launch_vjp_ymarch_t<true, false>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st);
+    }
+    return crk ? launch_vjp_ymarch_t<false, true>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st)
+               : launch_vjp_ymarch_t<false, false>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st);
 }
 
 cudaError_t launch_vjp_fp64(const GridGeom& g, const PhysD& q, bool crk, const AsmFields<double>& f,

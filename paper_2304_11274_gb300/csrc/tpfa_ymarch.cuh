@@ -95,9 +95,17 @@ struct YW {
     float c, m, p;
 };
 
-template <typename Real, bool DIAG, bool CRK, bool JAC, int W, bool JV = false>
+// v of one row for the adjoint as split doubles (hi + lo): the lane's cell
+// and the lane's halo cell (lanes 0 and 31); x-neighbours by shuffles where
+// used.
+struct YV {
+    F2Split c, h;
+};
+
+template <typename Real, bool DIAG, bool CRK, bool JAC, int W, bool JV = false, bool VJ = false>
 struct YMarch {
     static_assert(!JV || (sizeof(Real) == 4 && !JAC), "the J w march is the mixed path's, without CSR values");
+    static_assert(!VJ || (sizeof(Real) == 4 && !JAC && !JV), "the adjoint march is the mixed path's");
     using Phys = typename PhysOf<Real>::type;
     static constexpr int VEC = 16 / (int)sizeof(Real);  // elements per 16-byte store
 
@@ -172,7 +180,8 @@ struct YMarch {
     // ringm[s * 32 + l].  Slots rotate explicitly (no modulo per access).
     static constexpr int RING = 3;
     enum { F_P, F_Z, F_HP, F_HZ, F_TX, F_TY, F_TZ, F_TPP, F_TMP, F_PN, F_PHI, F_PZM, F_ZZM, F_TZM, F_PZP, F_ZZP,
-           F_HT1, F_HT2, NF };
+           F_HT1, F_HT2, F_K };
+    static constexpr int NF = VJ ? F_K + 1 : F_K;  // the adjoint also prefetches the cell's k
     Real* ring;      // RING * NF * 32 values
     double* ringm;   // RING * 32 values of m^n
     // J w mode: RING * NW * 32 values of w (own, halo, z-1, z+1), the
@@ -181,6 +190,11 @@ struct YMarch {
     double* ringw = nullptr;
     const double* wv = nullptr;
     double* Jw = nullptr;
+    // adjoint mode: k of the field type, the link geometry, the two gradients
+    const Real* kperm = nullptr;
+    LinkGeo lg{};
+    double* gP = nullptr;
+    double* gK = nullptr;
 
     __device__ __forceinline__ void cp4(Real* dst, const Real* src, bool valid) const {
         const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -227,7 +241,8 @@ struct YMarch {
             cp4(R + F_HT2 * 32, h2l ? f.Tpp + (c - nx - 1) : f.Tmp + (h2r ? c - nx + 1 : c), h2l || h2r);
         }
         cp8(ringm + sl * 32 + lane, f.mn + c, a);
-        if constexpr (JV) {
+        if constexpr (VJ) cp4(R + F_K * 32, kperm + c, a);
+        if constexpr (JV || VJ) {
             double* Wr = ringw + sl * (NW * 32) + lane;
             cp8(Wr, wv + c, a);
             cp8(Wr + 32, wv + ch, rv && hact);
@@ -278,6 +293,20 @@ struct YMarch {
         if (lane == 0) r.m = h;
         if (lane == 31) r.p = h;
         return r;
+    }
+
+    // v of the row in ring slot sl, split (own and halo).
+    __device__ __forceinline__ YV v_row(int sl) const {
+        const double* Wr = ringw + sl * (NW * 32) + lane;
+        return YV{split_f2(Wr[0]), split_f2(Wr[32])};
+    }
+    __device__ __forceinline__ F2Split v_minus(const YV& v) const {
+        F2Split t{__shfl_up_sync(0xffffffffu, v.c.hi, 1), __shfl_up_sync(0xffffffffu, v.c.lo, 1)};
+        return lane == 0 ? v.h : t;
+    }
+    __device__ __forceinline__ F2Split v_plus(const YV& v) const {
+        F2Split t{__shfl_down_sync(0xffffffffu, v.c.hi, 1), __shfl_down_sync(0xffffffffu, v.c.lo, 1)};
+        return lane == 31 ? v.h : t;
     }
 
     __device__ __forceinline__ YRow<Real> make_row(Real po, Real zo, Real ph, Real zh) const {
@@ -458,6 +487,74 @@ struct YMarch {
                 o.R[c] = r;
             }
             if (nonfinite(jw) || nonfinite(r)) atomicOr(o.status, STATUS_NONFINITE);
+        }
+        return U;
+    }
+
+    // Adjoint of row j (tpfa_vjp.cu states the formulation): vP, vC, vN hold
+    // v of rows j-1, j, j+1 split into FP32 pairs, vd the cell's own v and
+    // vzm, vzp the vertical neighbours' (FP64), kC the cell's k.  Per link,
+    // with dv = v_K - v_L (FP32 from the split pairs; FP64 then narrowed for
+    // the vertical links), the terms dF_KL/dp_K dv and F_KL (k_L / (k_K +
+    // k_L)) dv share one FP32x2 Kahan sum in slot order; k_L / (k_K + k_L) =
+    // Upsilon_KL (d/A) / (2 k_K) for the harmonic two-point transmissibility.
+    // A warp that meets a link with F == 0 (every exact tie) adds, for each
+    // link, v_L (dF_KL/dp_K + dF_LK/dp_K) with the second derivative
+    // evaluated from L's side (zero except at a tie).
+    template <int PATH>
+    __device__ __forceinline__ YUp<Real> row_vjp(int j, const YRow<Real>& P, const YRow<Real>& C,
+                                                 const YRow<Real>& N, const YIn<Real>& D, const YUp<Real>& Uprev,
+                                                 Real Ty_prev, Real Tpp_prev, Real Tmp_prev, const YV& vP,
+                                                 const YV& vC, const YV& vN, double vd, double vzm, double vzp,
+                                                 float kC) const {
+        const unsigned mask = row_mask<PATH>(j);
+        LinkOut<Real> S[NSLOT];
+        YUp<Real> U;
+        eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        Real Tx_m = vshfl_up(D.Tx), Tl = vshfl_up(Tpp_prev), Tr = vshfl_down(Tmp_prev);
+        if (lane == 0) Tx_m = D.hT1, Tl = D.hT2;
+        if (lane == 31) Tr = D.hT2;
+        const float Ts[NSLOT] = {D.Tz_m, Tl, Ty_prev, Tr, Tx_m, 0.f, D.Tx, D.Tmp, D.Ty, D.Tpp, D.Tz};
+        const float gs[NSLOT] = {lg.cz, lg.cd, lg.cy, lg.cd, lg.cx, 0.f, lg.cx, lg.cd, lg.cy, lg.cd, lg.cz};
+        const F2Split vs[NSLOT] = {F2Split{}, v_minus(vP), vP.c, v_plus(vP), v_minus(vC), F2Split{}, v_plus(vC),
+                                   v_minus(vN), vN.c, v_plus(vN), F2Split{}};
+        const float inv2k = kC > 0.f ? __fdiv_rn(0.5f, kC) : 0.f;
+        Kahan2 ks;
+        bool zero_flux = false;
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+            if (s == SLOT_SELF || !(mask & (1u << s))) continue;
+            const float dv = s == 0    ? narrow_rz(__dadd_rn(vd, -vzm))
+                             : s == 10 ? narrow_rz(__dadd_rn(vd, -vzp))
+                                       : diff_f2(vC.c, vs[s]);
+            const float ratio = __fmul_rn(__fmul_rn(Ts[s], gs[s]), inv2k);
+            ks.add(f2(__fmul_rn(S[s].Da, dv), __fmul_rn(__fmul_rn(S[s].F, ratio), dv)));
+            zero_flux |= S[s].F == 0.f;
+        }
+        double corr = 0.0;
+        if (__any_sync(0xffffffffu, zero_flux)) {
+            const CellVal<Real> zmc = make_cell(q, D.p_zm, D.z_zm);
+            const CellVal<Real> zpc = make_cell(q, D.p_zp, D.z_zp);
+            const CellVal<Real> nb[NSLOT] = {zmc, P.m, P.c, P.p, C.m, C.c, C.p, N.m, N.c, N.p, zpc};
+#pragma unroll
+            for (int s = 0; s < NSLOT; ++s) {
+                if (s == SLOT_SELF || !(mask & (1u << s))) continue;
+                const float dLK = link(q, Ts[s], nb[s], C.c).Db;
+                const double vL = s == 0    ? vzm
+                                  : s == 10 ? vzp
+                                            : __dadd_rn(widen(vs[s].hi), widen(vs[s].lo));
+                corr = __fma_rn(vL, widen(__fadd_rn(S[s].Da, dLK)), corr);
+            }
+        }
+        const AccF acc = accumulation<CRK>(q, C.c.p, D.pn, D.mn, C.c.rho, D.phi0);
+        if (act) {
+            const int c = kb + nx * j + i;
+            const double gp =
+                __dadd_rn(__fma_rn(vd, widen(acc.dA), __dadd_rn(widen(ks.s.x), -widen(ks.c.x))), corr);
+            const double gk = __dadd_rn(widen(ks.s.y), -widen(ks.c.y));
+            gP[c] = gp;
+            if (gK) gK[c] = gk;
+            if (nonfinite(gp) || nonfinite(gk)) atomicOr(o.status, STATUS_NONFINITE);
         }
         return U;
     }

@@ -59,6 +59,69 @@ def test_vjp_matches_oracle(shape, conn, precision, c_r):
         assert _normwise(g_lnk, g_lnk_ref) <= TOL[precision]
 
 
+VARIANT_SHAPES = [(1, 1, 1), (5, 1, 7), (33, 2, 1), (70, 41, 11), (72, 41, 11), (97, 70, 9)]
+
+
+@pytest.mark.parametrize("shape", VARIANT_SHAPES)
+@pytest.mark.parametrize("conn", [6, 10])
+@pytest.mark.parametrize("c_r", [0.0, 1e-9])
+def test_vjp_kernel_variants_bit_identical(shape, conn, c_r):
+    """The mixed path's adjoint: y-march and naive gather give identical bits
+    under every tiling the autotuner may pick."""
+    prob = synth.round_to_f32(synth.make_problem(*shape, seed=23, connectivity=conn, c_r=c_r))
+    v = synth.cotangent(prob.n, seed=8)
+    with _grid(prob, "mixed") as g:
+        g.set_state(prob.p, prob.pn)
+        gp_n, gk_n = (x.cpu().numpy() for x in g.vjp(v, kernel="naive"))
+        for JY, W in [(16, 4), (32, 8), (64, 4)]:
+            g.set_tiling(JY, W)
+            gp_t, gk_t = g.vjp(v, kernel="tiled")
+            g.sync_status()
+            assert np.array_equal(gp_t.cpu().numpy().view(np.uint64), gp_n.view(np.uint64)), (JY, W)
+            assert np.array_equal(gk_t.cpu().numpy().view(np.uint64), gk_n.view(np.uint64)), (JY, W)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kernel", ["naive", "tiled"])
+def test_vjp_every_link_a_tie(precision, kernel):
+    """Uniform pressure without gravity: dPhi = 0 on every link, so each row
+    takes the other cell's density and dF_Li/dp_i != -dF_iL/dp_i everywhere;
+    the gradient still matches the oracle (which evaluates each row from its
+    own side)."""
+    prob = synth.make_problem(37, 9, 6, seed=25, connectivity=10, g=0.0, c_f=1e-8, perturb=0.0)
+    prob.p = np.full(prob.n, 1.2e7)
+    v = synth.cotangent(prob.n, seed=9)
+    g_p_ref, g_lnk_ref = oracle.vjp(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                    prob.p, prob.pn, v)
+    if precision == "mixed":
+        prob.perm = prob.perm.astype(np.float32).astype(np.float64)
+        g_p_ref, g_lnk_ref = oracle.vjp(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                        prob.p, prob.pn, v)
+    with _grid(prob, precision) as g:
+        g.set_state(prob.p, prob.pn)
+        g_p, g_lnk = (x.cpu().numpy() for x in g.vjp(v, kernel=kernel))
+        g.sync_status()
+    assert _normwise(g_p, g_p_ref) <= TOL[precision]
+    assert np.abs(g_lnk).max() <= TOL[precision] * np.abs(g_p_ref).max()  # F = 0: no permeability gradient
+    assert np.abs(g_lnk_ref).max() == 0.0
+
+
+def test_vjp_smooth_cotangent_keeps_relative_accuracy():
+    """v = 1 + 1e-6 u: the permeability gradient depends only on the small
+    differences v_K - v_L, which the mixed path forms in FP64 before
+    narrowing, so its relative error stays at the FP32 level."""
+    prob = synth.round_to_f32(synth.make_problem(40, 37, 6, seed=27, connectivity=10))
+    prob.perm = prob.perm.astype(np.float32).astype(np.float64)
+    v = 1.0 + 1e-6 * synth.cotangent(prob.n, seed=10)
+    g_p_ref, g_lnk_ref = oracle.vjp(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                    prob.p, prob.pn, v)
+    with _grid(prob, "mixed") as g:
+        g.set_state(prob.p, prob.pn)
+        g_p, g_lnk = (x.cpu().numpy() for x in g.vjp(v))
+    assert _normwise(g_lnk, g_lnk_ref) <= 1e-6
+    assert _normwise(g_p, g_p_ref) <= 1e-6
+
+
 def test_vjp_adjoint_size_against_oracle():
     """128^3 with 10 links on the mixed path: the adjoint workload's grid."""
     prob = synth.round_to_f32(synth.config_problem(4))

@@ -156,3 +156,40 @@ def test_jvp_errors():
         with pytest.raises(ValueError):
             g.jvp(np.zeros(prob.n + 1))
         assert g.lib.tpfa_jvp(g.handle, None, None, None, None) == -1  # TPFA_ERR_INVALID_ARG
+
+
+@pytest.mark.slow
+def test_jvp_full_size_sampled():
+    """512 x 512 x 256, 10 links, mixed, autotuned tiling (the benchmark's
+    J w launch): sampled rows against the oracle row of each cell's clipped
+    3 x 3 x 3 box dotted with w, plus the eight corners."""
+    from paper_2304_11274_gb300.api import Grid
+    prob = synth.round_to_f32(synth.config_problem(1))
+    w = synth.cotangent(prob.n, synth.BASE_SEED + 40)
+    rng = np.random.default_rng(5)
+    nx, ny, nz = prob.nx, prob.ny, prob.nz
+    cells = [(i, j, k) for i in (0, nx - 1) for j in (0, ny - 1) for k in (0, nz - 1)]
+    cells += [(int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))) for _ in range(3000)]
+    with Grid(nx, ny, nz, prob.phys, "mixed", prob.perm, prob.poro, prob.depth) as g:
+        g.set_state(prob.p, prob.pn)
+        g.autotune(None)
+        Jw, _ = g.jvp(w)
+        g.sync_status()
+        lin = np.array([i + nx * (j + ny * k) for (i, j, k) in cells])
+        got = Jw[torch.as_tensor(lin, device="cuda")].cpu().numpy()
+        del Jw
+    worst, skipped = 0.0, 0
+    for n, (i, j, k) in enumerate(cells):
+        c = lin[n]
+        _, Jrow, dphi = C.subgrid_row(prob, i, j, k)
+        amb = any(abs(dphi[L]) <= 32 * C.EPS32 * (abs(prob.p[c] - prob.p[L]) +
+                                                 1.1e3 * 9.81 * abs(prob.depth[c] - prob.depth[L]))
+                  for L in Jrow if L != c)
+        if amb:
+            skipped += 1
+            continue
+        ref = sum(Jrow[L] * w[L] for L in Jrow)
+        scale = sum(abs(Jrow[L] * w[L]) for L in Jrow)
+        worst = max(worst, abs(got[n] - ref) / scale)
+    assert worst <= TOL["mixed"], worst
+    assert skipped <= len(cells) // 100
