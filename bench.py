@@ -55,6 +55,25 @@ def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
+FP64_PEAK_TOPS = 0.625  # nominal GB300 FP64: 1.25 TFLOP/s, i.e. 0.625 T FMA instructions/s
+
+
+def fp64_ops_per_cell():
+    """FP64 instructions per cell of the FP64 assembly kernel, from the
+    committed ncu count (None if absent)."""
+    path = os.path.join(ROOT, "profiles", "assemble_fp64_256x256x128_ops.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            if line.strip().startswith("- `fp64_ops_per_cell`"):
+                try:
+                    return float(line.split("`")[3])
+                except (IndexError, ValueError):
+                    return None
+    return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -220,6 +239,8 @@ def run_ours(args):
     # roofline of the assembly kernel (the only kernel in the step)
     nbytes = algorithmic_bytes(prob.n, g.nnz, "mixed")
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    launch_stats = {"mean_ms": statistics.mean(launch_ms), "sd_ms": statistics.pstdev(launch_ms),
+                    "min_ms": min(launch_ms), "max_ms": max(launch_ms)}
     peak, peak_kind = measured_peaks()
     achieved = nbytes / avg_launch_s / 1e9
     khash = kernel_source_hash()
@@ -275,8 +296,15 @@ def run_ours(args):
         g64.sync_status()
         f_ms = a.elapsed_time(b) / nf
         b64 = algorithmic_bytes(prob.n, g64.nnz, "fp64")
-        fp64 = {"value": prob.n / (f_ms * 1e-3), "unit": "cells/s", "ms_per_step": f_ms,
+        ops = fp64_ops_per_cell()
+        rate = prob.n / (f_ms * 1e-3)
+        fp64 = {"value": rate, "unit": "cells/s", "ms_per_step": f_ms,
                 "hbm_GBps": b64 / (f_ms * 1e-3) / 1e9, "hbm_frac": b64 / (f_ms * 1e-3) / 1e9 / peak,
+                "fp64_roofline": None if ops is None else {
+                    "bound": "fp64", "ops_per_cell": ops, "achieved": rate * ops / 1e12, "peak": FP64_PEAK_TOPS,
+                    "unit": "T FP64 instructions/s", "frac": rate * ops / 1e12 / FP64_PEAK_TOPS,
+                    "peak_kind": "nominal (1.25 TFLOP/s, an FMA counted once)",
+                    "ops_source": "ncu count in profiles/assemble_fp64_256x256x128_ops.md"},
                 "note": "plain FP64 path, same grid; bound by the FP64 pipe, not HBM"}
         g64.close()
 
@@ -307,6 +335,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
                      "kernel": "k_assemble_ymarch<float,DIAG,!CR,JAC>", "kernel_source_sha256_16": khash},
+        "launch_ms": launch_stats,
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": args.steps,

@@ -289,3 +289,24 @@ def test_full_size_layered_grid_sampled(precision):
     eR, eJ, skipped, n = _sampled_rows(prob, precision, 2000, seed=2)
     assert eR <= TOL[precision] and eJ <= TOL[precision], (eR, eJ)
     assert skipped <= n // 100
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_precision_study_layered_full_grid(precision):
+    """The precision study on every row of the 256^3 layered medium (log10 k
+    per layer ~ U[-18, -12], 5e6 to 3e7 Pa): normwise residual and row-wise
+    Jacobian errors within the bars, and the max / RMS entrywise relative
+    error printed for the record."""
+    prob = synth.config_problem(2)
+    if precision == "mixed":
+        prob = synth.round_to_f32(prob)
+    out = run_gpu(prob, precision)
+    ref = C.reference(prob, EPS[precision])
+    J = gpu_jacobian_f64(out, ref)
+    eR = C.residual_error(out["R"], ref)
+    eJ = C.jacobian_row_error(J, ref)
+    emax, erms = C.entry_stats(J, ref)
+    print(f"\nprecision study 256^3 layered {precision}: residual {eR:.3e}, jacobian row {eJ:.3e}, "
+          f"entrywise max {emax:.3e} rms {erms:.3e}, ambiguous links {int(ref['ambiguous'].sum())}")
+    assert eR <= TOL[precision] and eJ <= TOL[precision], (eR, eJ)
