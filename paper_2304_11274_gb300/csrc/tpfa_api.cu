@@ -119,6 +119,7 @@ struct tpfa_grid {
     double* kv_diag = nullptr;
     double* kv_R = nullptr;
     double* kv_vec[10] = {};  // x, r, r^, p, p^, v, s, s^, t, M^-1
+    float* kv_f32[4] = {};    // p^ and s^ split into FP32 pairs (mixed path)
     double* kv_part = nullptr;
     KrylovScalars* kv_S = nullptr;
     KrylovScalars* kv_S_host = nullptr;  // pinned
@@ -135,6 +136,7 @@ struct tpfa_grid {
         dev_free(kv_diag);
         dev_free(kv_R);
         for (auto& v : kv_vec) dev_free(v), v = nullptr;
+        for (auto& v : kv_f32) dev_free(v), v = nullptr;
         dev_free(kv_part);
         dev_free(kv_S);
         if (kv_S_host) cudaFreeHost(kv_S_host);
@@ -230,6 +232,8 @@ int krylov_workspace(tpfa_grid* h) {
     if (ok && h->prec == TPFA_MIXED) ok = dev_alloc((void**)&h->kv_diag, nb) == cudaSuccess;
     ok = ok && dev_alloc((void**)&h->kv_R, nb) == cudaSuccess;
     for (auto& v : h->kv_vec) ok = ok && dev_alloc((void**)&v, nb) == cudaSuccess;
+    if (h->prec == TPFA_MIXED)
+        for (auto& v : h->kv_f32) ok = ok && dev_alloc((void**)&v, sizeof(float) * (size_t)h->N) == cudaSuccess;
     ok = ok && dev_alloc((void**)&h->kv_part, sizeof(double) * 2 * (size_t)krylov_partials(h->geom, h->N)) ==
                    cudaSuccess;
     ok = ok && dev_alloc((void**)&h->kv_S, sizeof(KrylovScalars)) == cudaSuccess;
@@ -240,6 +244,7 @@ int krylov_workspace(tpfa_grid* h) {
         dev_free(h->kv_diag);
         dev_free(h->kv_R);
         for (auto& v : h->kv_vec) dev_free(v), v = nullptr;
+        for (auto& v : h->kv_f32) dev_free(v), v = nullptr;
         dev_free(h->kv_part);
         dev_free(h->kv_S);
         if (h->kv_S_host) cudaFreeHost(h->kv_S_host);
@@ -268,6 +273,10 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     w.sh = h->kv_vec[7];
     w.t = h->kv_vec[8];
     w.dinv = h->kv_vec[9];
+    w.phh = h->kv_f32[0];
+    w.phl = h->kv_f32[1];
+    w.shh = h->kv_f32[2];
+    w.shl = h->kv_f32[3];
     w.part = h->kv_part;
     w.S = h->kv_S;
     KrylovScalars* Sh = h->kv_S_host;

@@ -72,6 +72,7 @@ struct KrylovScalars {
 };
 struct KrylovWork {
     double *x, *r, *rh, *p, *ph, *v, *s, *sh, *t, *dinv;
+    float *phh, *phl, *shh, *shl;  // p^ and s^ split into FP32 pairs (mixed path), else null
     double* part;  // 2 * krylov_partials() per-block partial sums
     KrylovScalars* S;
 };

@@ -18,8 +18,11 @@
 //
 // The matrix-vector product walks the structured stencil: row (i, j, k)
 // starts at the closed-form offset of the pattern and its columns follow the
-// slot order, so neither row_ptr nor col_idx is read.  Products and sums are
-// FP64 (FP32 values are widened exactly on the integer pipe).
+// slot order, so neither row_ptr nor col_idx is read.  FP64 path: products
+// and sums in FP64.  Mixed path: the FP32 off-diagonal values times the
+// vector split into FP32 pairs (written by the update kernels), exact
+// two-float products summed as a double-float, plus the FP64 diagonal times
+// the FP64 vector.
 #include <cuda_runtime.h>
 
 #include "tpfa_impl.h"
@@ -100,6 +103,55 @@ __global__ void __launch_bounds__(256) k_spmv(GridGeom g, const Real* __restrict
     block_partials(d0, d1, part, b);
 }
 
+// Mixed path: y = J x with x given as split pairs x = hi + lo (FP32) and the
+// FP32 off-diagonals a: each a hi is formed exactly as p + e (e = fma(a, hi,
+// -p)), a lo is added to e, and the terms are summed as a double-float
+// (TwoSum on the leading parts, the trailing parts summed apart), about 48
+// bits; the FP64 diagonal times the FP64 x is added in FP64.  Three FP64
+// operations per row instead of eleven, the product as accurate as an FP64
+// one for the Krylov iteration.
+__global__ void __launch_bounds__(256) k_spmv_mixed(GridGeom g, const float* __restrict__ vals,
+                                                    const double* __restrict__ diag64, const double* __restrict__ x,
+                                                    const float* __restrict__ xhi, const float* __restrict__ xlo,
+                                                    double* __restrict__ y, const double* __restrict__ a, double* part,
+                                                    const KrylovScalars* S) {
+    if (S->done) return;  // uniform over the grid
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z;
+    double d0 = 0.0, d1 = 0.0;
+    if (i < g.nx && j < g.ny) {
+        const int nx = g.nx, nxy = nx * g.ny;
+        const int c = i + nx * j + nxy * k;
+        const unsigned mask = slot_mask(g, i, j, k);
+        const int off[NSLOT] = {-nxy, -nx - 1, -nx, -nx + 1, -1, 0, 1, nx - 1, nx, nx + 1, nxy};
+        const float* row = vals + row_start(g, i, j, k);
+        float ah = 0.f, al = 0.f;
+        int pos = 0;
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+            if (!(mask & (1u << s))) continue;
+            if (s != SLOT_SELF) {
+                const float av = row[pos], xh = xhi[c + off[s]], xl = xlo[c + off[s]];
+                const float p = __fmul_rn(av, xh);
+                const float t = __fmaf_rn(av, xl, __fmaf_rn(av, xh, -p));
+                const float sum = __fadd_rn(ah, p);
+                const float bb = __fsub_rn(sum, ah);
+                const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+                ah = sum;
+                al = __fadd_rn(al, __fadd_rn(err, t));
+            }
+            ++pos;
+        }
+        const double yc = __fma_rn(diag64[c], x[c], __dadd_rn(widen(ah), widen(al)));
+        y[c] = yc;
+        d0 = a[c] * yc;
+        d1 = yc * yc;
+    }
+    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    block_partials(d0, d1, part, b);
+}
+
 // M^-1 = 1 / diag(J) (1 where the diagonal is zero).
 template <typename Real, bool MIXED>
 __global__ void __launch_bounds__(256) k_dinv(GridGeom g, const Real* __restrict__ vals,
@@ -137,7 +189,8 @@ __global__ void __launch_bounds__(kVecThreads) k_init(long long n, const double*
 // p = r + beta (p - omega v) (p = r on the first pass), p^ = M^-1 p.
 __global__ void __launch_bounds__(kVecThreads) k_update_p(long long n, const double* __restrict__ r,
                                                           const double* __restrict__ v, double* __restrict__ p,
-                                                          double* __restrict__ ph, const double* __restrict__ dinv,
+                                                          double* __restrict__ ph, float* __restrict__ phh,
+                                                          float* __restrict__ phl, const double* __restrict__ dinv,
                                                           const KrylovScalars* S) {
     if (S->done) return;
     const bool first = S->iter == 0;
@@ -145,21 +198,34 @@ __global__ void __launch_bounds__(kVecThreads) k_update_p(long long n, const dou
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const double pc = first ? r[c] : fma(beta, fma(-omega, v[c], p[c]), r[c]);
         p[c] = pc;
-        ph[c] = pc * dinv[c];
+        const double phc = pc * dinv[c];
+        ph[c] = phc;
+        if (phh) {
+            const F2Split sp = split_f2(phc);
+            phh[c] = sp.hi;
+            phl[c] = sp.lo;
+        }
     }
 }
 
 // s = r - alpha v, s^ = M^-1 s.
 __global__ void __launch_bounds__(kVecThreads) k_update_s(long long n, const double* __restrict__ r,
                                                           const double* __restrict__ v, double* __restrict__ s,
-                                                          double* __restrict__ sh, const double* __restrict__ dinv,
+                                                          double* __restrict__ sh, float* __restrict__ shh,
+                                                          float* __restrict__ shl, const double* __restrict__ dinv,
                                                           const KrylovScalars* S) {
     if (S->done) return;
     const double alpha = S->alpha;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const double sc = fma(-alpha, v[c], r[c]);
         s[c] = sc;
-        sh[c] = sc * dinv[c];
+        const double shc = sc * dinv[c];
+        sh[c] = shc;
+        if (shh) {
+            const F2Split sp = split_f2(shc);
+            shh[c] = sp.hi;
+            shl[c] = sp.lo;
+        }
     }
 }
 
@@ -304,15 +370,17 @@ cudaError_t krylov_iteration(const GridGeom& g, long long n, bool mixed, const v
     const long long nb = krylov_vec_blocks(n);
     const dim3 sg = stencil_grid(g), blk(32, 8, 1);
     const long long ns = (long long)sg.x * sg.y * sg.z;
-    k_update_p<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.r, w.v, w.p, w.ph, w.dinv, w.S);
+    k_update_p<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.r, w.v, w.p, w.ph, mixed ? w.phh : nullptr,
+                                                     mixed ? w.phl : nullptr, w.dinv, w.S);
     if (mixed)
-        k_spmv<float, true><<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.ph, w.v, w.rh, w.part, w.S);
+        k_spmv_mixed<<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.ph, w.phh, w.phl, w.v, w.rh, w.part, w.S);
     else
         k_spmv<double, false><<<sg, blk, 0, st>>>(g, (const double*)vals, diag64, w.ph, w.v, w.rh, w.part, w.S);
     k_finalize<<<1, kFinThreads, 0, st>>>(w.part, ns, 1, w.S);
-    k_update_s<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.r, w.v, w.s, w.sh, w.dinv, w.S);
+    k_update_s<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.r, w.v, w.s, w.sh, mixed ? w.shh : nullptr,
+                                                     mixed ? w.shl : nullptr, w.dinv, w.S);
     if (mixed)
-        k_spmv<float, true><<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.sh, w.t, w.s, w.part, w.S);
+        k_spmv_mixed<<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.sh, w.shh, w.shl, w.t, w.s, w.part, w.S);
     else
         k_spmv<double, false><<<sg, blk, 0, st>>>(g, (const double*)vals, diag64, w.sh, w.t, w.s, w.part, w.S);
     k_finalize<<<1, kFinThreads, 0, st>>>(w.part, ns, 2, w.S);
