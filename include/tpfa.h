@@ -271,7 +271,9 @@ int tpfa_autotune(tpfa_handle h, const char* cache_path, void* stream);
  * One Newton iteration on the backward-Euler system Eq. vk (R(p^{n+1}) = 0):
  *   assemble R(p^k) and J = dR/dp at p^k (the fused kernel of
  *   tpfa_assemble_jacobian), solve J delta = -R with BiCGStab right-
- *   preconditioned by the Jacobi (diagonal) preconditioner, p^{k+1} = p^k + delta.
+ *   preconditioned by the tridiagonal part of J along z (each (i, j) column's
+ *   vertical couplings, solved exactly; the vertical links of thin cells
+ *   dominate) or by its diagonal, p^{k+1} = p^k + delta.
  * The paper names the implicit system and a Krylov solve of it as the use of
  * the flux operator but fixes neither the nonlinear nor the linear method;
  * these are the standard choices.  Vectors, dot products and the update are
@@ -281,10 +283,14 @@ int tpfa_autotune(tpfa_handle h, const char* cache_path, void* stream);
  * solver's scalars live on the device: the host reads them every
  * `check_every` iterations.
  */
+#define TPFA_PRECOND_ZLINE 0  /* tridiagonal part of J along z, solved exactly per (i, j) column */
+#define TPFA_PRECOND_JACOBI 1 /* diagonal of J */
+
 typedef struct {
-    int max_iters;    /* BiCGStab iteration limit (<= 0: 1000) */
-    double rtol;      /* stop when ||b - J x||_2 <= rtol ||b||_2 (<= 0: 1e-8) */
-    int check_every;  /* iterations between host convergence checks (<= 0: 8) */
+    int max_iters;      /* BiCGStab iteration limit (<= 0: 1000) */
+    double rtol;        /* stop when ||b - J x||_2 <= rtol ||b||_2 (<= 0: 1e-8) */
+    int check_every;    /* iterations between host convergence checks (<= 0: 8) */
+    int preconditioner; /* TPFA_PRECOND_ZLINE (default, 0) or TPFA_PRECOND_JACOBI */
 } tpfa_krylov_opts;
 
 typedef struct {
@@ -301,7 +307,8 @@ typedef struct {
  * (device, caller-owned).  opts may be NULL (defaults); stats may be NULL.
  * Synchronous on `stream`.  Returns TPFA_ERR_NO_CONVERGENCE when the
  * tolerance was not met (x_dev then holds the last iterate).  The first
- * call allocates the workspace: nnz values, 10 FP64 vectors of N.
+ * call allocates the workspace: nnz values, 12 FP64 vectors of N (and, on
+ * TPFA_MIXED, four FP32 vectors).
  */
 int tpfa_linear_solve(tpfa_handle h, const double* b_dev, double* x_dev, const tpfa_krylov_opts* opts,
                       tpfa_krylov_stats* stats, void* stream);

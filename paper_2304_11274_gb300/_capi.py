@@ -25,6 +25,7 @@ ERRORS = {
 }
 TPFA_FP64, TPFA_MIXED = 0, 1
 KERNELS = {"auto": 0, "naive": 1, "tiled": 2}
+PRECONDITIONERS = {"zline": 0, "jacobi": 1}
 
 
 class TPFAError(RuntimeError):
@@ -51,7 +52,8 @@ class TPFAParams(ctypes.Structure):
 
 
 class TPFAKrylovOpts(ctypes.Structure):
-    _fields_ = [("max_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("check_every", ctypes.c_int)]
+    _fields_ = [("max_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("check_every", ctypes.c_int),
+                ("preconditioner", ctypes.c_int)]
 
 
 class TPFAKrylovStats(ctypes.Structure):

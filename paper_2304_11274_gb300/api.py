@@ -183,23 +183,24 @@ class Grid:
         return Jw, R
 
     @staticmethod
-    def _krylov(rtol, max_iters, check_every):
-        return _capi.TPFAKrylovOpts(int(max_iters), float(rtol), int(check_every))
+    def _krylov(rtol, max_iters, check_every, precond="zline"):
+        return _capi.TPFAKrylovOpts(int(max_iters), float(rtol), int(check_every), _capi.PRECONDITIONERS[precond])
 
     @staticmethod
     def _stats(st):
         return {k: getattr(st, k) for k, _ in _capi.TPFAKrylovStats._fields_}
 
-    def linear_solve(self, b, rtol=1e-8, max_iters=1000, check_every=8, out=None, stream=None):
-        """x with J x = b (J at the bound state; Jacobi-preconditioned
-        BiCGStab, FP64 vectors).  Returns (x, stats); raises TPFAError
-        (TPFA_ERR_NO_CONVERGENCE) if the tolerance is not met."""
+    def linear_solve(self, b, rtol=1e-8, max_iters=1000, check_every=8, precond="zline", out=None, stream=None):
+        """x with J x = b (J at the bound state; BiCGStab preconditioned by
+        the z-line ("zline") or diagonal ("jacobi") part of J, FP64 vectors).
+        Returns (x, stats); raises TPFAError (TPFA_ERR_NO_CONVERGENCE) if the
+        tolerance is not met."""
         b = _dev_f64(b, self.device)
         if b.numel() != self.n:
             raise ValueError(f"expected {self.n} values, got {b.numel()}")
         x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
         st = _capi.TPFAKrylovStats()
-        opts = self._krylov(rtol, max_iters, check_every)
+        opts = self._krylov(rtol, max_iters, check_every, precond)
         rc = self.lib.tpfa_linear_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(st),
                                         _stream(stream))
         self.last_stats = self._stats(st)
@@ -207,7 +208,7 @@ class Grid:
         return x, self.last_stats
 
     def newton_step(self, p, rtol=1e-8, max_iters=1000, check_every=8, want_residual=False, want_delta=False,
-                    stream=None):
+                    precond="zline", stream=None):
         """One Newton step of Eq. vk in place on p (a device tensor of the
         field dtype, bound as the pressure).  Returns (stats, R(p) or None,
         delta or None)."""
@@ -217,7 +218,7 @@ class Grid:
         R = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_residual else None
         d = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_delta else None
         st = _capi.TPFAKrylovStats()
-        opts = self._krylov(rtol, max_iters, check_every)
+        opts = self._krylov(rtol, max_iters, check_every, precond)
         self._p = p
         rc = self.lib.tpfa_newton_step(self.handle, _ptr(p), ctypes.byref(opts), ctypes.byref(st), _ptr(R),
                                        _ptr(d), _stream(stream))

@@ -118,7 +118,7 @@ struct tpfa_grid {
     void* kv_vals = nullptr;
     double* kv_diag = nullptr;
     double* kv_R = nullptr;
-    double* kv_vec[10] = {};  // x, r, r^, p, p^, v, s, s^, t, M^-1
+    double* kv_vec[12] = {};  // x, r, r^, p, p^, v, s, s^, t, M^-1 (and z-line multipliers, super-diagonal)
     float* kv_f32[4] = {};    // p^ and s^ split into FP32 pairs (mixed path)
     double* kv_part = nullptr;
     KrylovScalars* kv_S = nullptr;
@@ -223,7 +223,7 @@ int march_rows(const tpfa_grid* h) {
     return jy;
 }
 
-// Newton / Krylov workspace: the assembled Jacobian, R, ten FP64 vectors,
+// Newton / Krylov workspace: the assembled Jacobian, R, twelve FP64 vectors,
 // the partial sums and the scalar record (device and pinned host copies).
 int krylov_workspace(tpfa_grid* h) {
     if (h->kv_S_host) return TPFA_OK;
@@ -261,6 +261,7 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 1000;
     const double rtol = (opts && opts->rtol > 0.0) ? opts->rtol : 1e-8;
     const int every = (opts && opts->check_every > 0) ? opts->check_every : 8;
+    const bool line = !(opts && opts->preconditioner == TPFA_PRECOND_JACOBI);
     const bool mixed = h->prec == TPFA_MIXED;
     KrylovWork w;
     w.x = x;
@@ -273,6 +274,8 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     w.sh = h->kv_vec[7];
     w.t = h->kv_vec[8];
     w.dinv = h->kv_vec[9];
+    w.lmul = h->kv_vec[10];
+    w.up = h->kv_vec[11];
     w.phh = h->kv_f32[0];
     w.phl = h->kv_f32[1];
     w.shh = h->kv_f32[2];
@@ -284,7 +287,7 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     Sh->tol2 = rtol * rtol;
     Sh->max_iters = max_iters;
     cudaError_t e = cudaMemcpyAsync(w.S, Sh, sizeof(KrylovScalars), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = krylov_dinv(h->geom, mixed, h->kv_vals, h->kv_diag, w.dinv, st);
+    if (e == cudaSuccess) e = krylov_dinv(h->geom, mixed, h->kv_vals, h->kv_diag, w.dinv, w.lmul, w.up, line, st);
     if (e == cudaSuccess) e = krylov_start(h->geom, h->N, b, sign, w, st);
     if (e != cudaSuccess) return cuda_fail(e, "Krylov start");
     // every kernel returns at entry once `done` is set, so batches of
@@ -293,7 +296,7 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     // max_iters / every + 1 polls
     for (int it = 0; it <= max_iters + every; it += every) {
         for (int q = 0; q < every && e == cudaSuccess; ++q)
-            e = krylov_iteration(h->geom, h->N, mixed, h->kv_vals, h->kv_diag, w, st);
+            e = krylov_iteration(h->geom, h->N, mixed, h->kv_vals, h->kv_diag, w, line, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(Sh, w.S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "Krylov iteration");

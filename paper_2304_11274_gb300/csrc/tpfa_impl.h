@@ -73,18 +73,21 @@ struct KrylovScalars {
 struct KrylovWork {
     double *x, *r, *rh, *p, *ph, *v, *s, *sh, *t, *dinv;
     float *phh, *phl, *shh, *shl;  // p^ and s^ split into FP32 pairs (mixed path), else null
-    double* part;  // 2 * krylov_partials() per-block partial sums
+    double *lmul, *up;  // z-line factorisation: multipliers and super-diagonal
+    double* part;       // 2 * krylov_partials() per-block partial sums
     KrylovScalars* S;
 };
 long long krylov_vec_blocks(long long n);
 long long krylov_partials(const GridGeom& g, long long n);
+// M^-1 data: the inverse diagonal (Jacobi) or the inverse pivots of the z-line
+// factorisation (line).
 cudaError_t krylov_dinv(const GridGeom& g, bool mixed, const void* vals, const double* diag64, double* dinv,
-                        cudaStream_t st);
+                        double* lmul, double* up, bool line, cudaStream_t st);
 // x = 0, r = r^ = sign * b, scalars initialised (S->tol2, S->max_iters set by the caller)
 cudaError_t krylov_start(const GridGeom& g, long long n, const double* b, double sign, const KrylovWork& w,
                          cudaStream_t st);
 cudaError_t krylov_iteration(const GridGeom& g, long long n, bool mixed, const void* vals, const double* diag64,
-                             const KrylovWork& w, cudaStream_t st);
+                             const KrylovWork& w, bool line, cudaStream_t st);
 cudaError_t krylov_add_delta(long long n, bool mixed, void* p, const double* d, cudaStream_t st);
 
 // General meshes (tpfa_mesh.cu).

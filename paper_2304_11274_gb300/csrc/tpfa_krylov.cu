@@ -1,7 +1,8 @@
 // tpfa_krylov.cu -- Jacobi-preconditioned BiCGStab on the assembled Jacobian
 // (the linear solve of a Newton step on Eq. vk), sm_103a.
 //
-// BiCGStab (van der Vorst, 1992) with right preconditioning by M = diag(J):
+// BiCGStab (van der Vorst, 1992) with right preconditioning by M, the
+// tridiagonal part of J along z (default) or its diagonal (Jacobi):
 //   r = b, r^ = b, x = 0, rho = (r^, r)
 //   repeat:  p = r + beta (p - omega v)            (p = r on the first pass)
 //            p^ = M^-1 p,  v = J p^,  alpha = rho / (r^, v)
@@ -171,6 +172,129 @@ __global__ void __launch_bounds__(256) k_dinv(GridGeom g, const Real* __restrict
     dinv[c] = d != 0.0 ? 1.0 / d : 1.0;
 }
 
+// ---------------------------------------------------------------- z-line preconditioner
+//
+// M = the tridiagonal part of J along z (each cell's diagonal and its two
+// vertical couplings), inverted exactly column by column with the Thomas
+// algorithm: the vertical links of 10 x 10 x 2 m cells carry 25 times the
+// transmissibility of the horizontal ones, so M captures most of J.  The
+// factorisation (once per solve) stores three coalesced per-cell arrays:
+// the elimination multiplier l_k = sub_k / b'_{k-1}, the super-diagonal
+// u_k and the inverse pivot 1 / b'_k.  An application is one thread per
+// (i, j) column, a forward sweep y_k = in_k - l_k y_{k-1} and a backward
+// sweep z_k = (y_k - u_k z_{k+1}) / b'_k, each loading the next chunk of
+// steps while it computes the current one.
+
+constexpr int kLineThreads = 64;
+constexpr int kChunk = 8;
+
+template <typename Real, bool MIXED>
+__global__ void __launch_bounds__(kLineThreads) k_line_factor(GridGeom g, const Real* __restrict__ vals,
+                                                              const double* __restrict__ diag64,
+                                                              double* __restrict__ inv_b, double* __restrict__ lmul,
+                                                              double* __restrict__ up) {
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (col >= nxy) return;
+    const int i = (int)(col % g.nx), j = (int)(col / g.nx);
+    double inv_prev = 0.0, sup_prev = 0.0;
+    for (int k = 0; k < g.nz; ++k) {
+        const long long c = col + nxy * k;
+        const long long rs = row_start(g, i, j, k);
+        const unsigned mask = slot_mask(g, i, j, k);
+        const double diag = MIXED ? diag64[c] : as_f64(vals[rs + slot_pos(mask, SLOT_SELF)]);
+        double b = diag, l = 0.0;
+        if (k > 0) {
+            l = as_f64(vals[rs]) * inv_prev;
+            b = fma(-l, sup_prev, diag);
+        }
+        const double inv = b != 0.0 ? 1.0 / b : 1.0;
+        const double sup = k + 1 < g.nz ? as_f64(vals[rs + __popc(mask) - 1]) : 0.0;
+        inv_b[c] = inv;
+        lmul[c] = l;
+        up[c] = sup;
+        sup_prev = sup;
+        inv_prev = inv;
+    }
+}
+
+struct LineChunk {
+    double a[kChunk], b[kChunk], d[kChunk];
+};
+
+// out = M^-1 in; on the mixed path also out split into FP32 pairs.
+__global__ void __launch_bounds__(kLineThreads) k_line_apply(GridGeom g, const double* __restrict__ inv_b,
+                                                             const double* __restrict__ lmul,
+                                                             const double* __restrict__ up,
+                                                             const double* __restrict__ in, double* __restrict__ out,
+                                                             float* __restrict__ hi, float* __restrict__ lo,
+                                                             const KrylovScalars* S) {
+    if (S->done) return;
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (col >= nxy) return;
+    const int nz = g.nz;
+    const int nch = (nz + kChunk - 1) / kChunk;
+    // forward: y_k = in_k - l_k y_{k-1}
+    auto load_f = [&](int q, LineChunk& L) {
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            const int k = q * kChunk + u;
+            const bool ok = k < nz;
+            const long long c = col + nxy * (ok ? k : 0);
+            L.a[u] = ok ? in[c] : 0.0;
+            L.b[u] = ok ? lmul[c] : 0.0;
+        }
+    };
+    LineChunk A, B;
+    load_f(0, A);
+    double y = 0.0;
+    for (int q = 0; q < nch; ++q) {
+        if (q + 1 < nch) load_f(q + 1, B);
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            const int k = q * kChunk + u;
+            if (k < nz) {
+                y = fma(-A.b[u], y, A.a[u]);
+                out[col + nxy * k] = y;
+            }
+        }
+        A = B;
+    }
+    // back: z_k = (y_k - u_k z_{k+1}) / b'_k, steps k = nz-1 down to 0
+    auto load_b = [&](int q, LineChunk& L) {
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            const int k = nz - 1 - (q * kChunk + u);
+            const bool ok = k >= 0;
+            const long long c = col + nxy * (ok ? k : 0);
+            L.a[u] = ok ? out[c] : 0.0;
+            L.b[u] = ok ? up[c] : 0.0;
+            L.d[u] = ok ? inv_b[c] : 0.0;
+        }
+    };
+    load_b(0, A);
+    double z = 0.0;
+    for (int q = 0; q < nch; ++q) {
+        if (q + 1 < nch) load_b(q + 1, B);
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            const int k = nz - 1 - (q * kChunk + u);
+            if (k >= 0) {
+                z = fma(-A.b[u], z, A.a[u]) * A.d[u];
+                const long long c = col + nxy * k;
+                out[c] = z;
+                if (hi) {
+                    const F2Split sp = split_f2(z);
+                    hi[c] = sp.hi;
+                    lo[c] = sp.lo;
+                }
+            }
+        }
+        A = B;
+    }
+}
+
 // x = 0, r = r^ = sign * b; partials of (b, b).
 __global__ void __launch_bounds__(kVecThreads) k_init(long long n, const double* __restrict__ b, double sign,
                                                       double* __restrict__ x, double* __restrict__ r,
@@ -198,6 +322,7 @@ __global__ void __launch_bounds__(kVecThreads) k_update_p(long long n, const dou
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const double pc = first ? r[c] : fma(beta, fma(-omega, v[c], p[c]), r[c]);
         p[c] = pc;
+        if (!dinv) continue;  // the line preconditioner writes p^
         const double phc = pc * dinv[c];
         ph[c] = phc;
         if (phh) {
@@ -219,6 +344,7 @@ __global__ void __launch_bounds__(kVecThreads) k_update_s(long long n, const dou
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const double sc = fma(-alpha, v[c], r[c]);
         s[c] = sc;
+        if (!dinv) continue;  // the line preconditioner writes s^
         const double shc = sc * dinv[c];
         sh[c] = shc;
         if (shh) {
@@ -350,10 +476,25 @@ long long krylov_partials(const GridGeom& g, long long n) {
 }
 
 cudaError_t krylov_dinv(const GridGeom& g, bool mixed, const void* vals, const double* diag64, double* dinv,
-                        cudaStream_t st) {
+                        double* lmul, double* up, bool line, cudaStream_t st) {
+    if (line) {
+        const unsigned nb = (unsigned)(((long long)g.nx * g.ny + kLineThreads - 1) / kLineThreads);
+        if (mixed)
+            k_line_factor<float, true><<<nb, kLineThreads, 0, st>>>(g, (const float*)vals, diag64, dinv, lmul, up);
+        else
+            k_line_factor<double, false><<<nb, kLineThreads, 0, st>>>(g, (const double*)vals, diag64, dinv, lmul, up);
+        return cudaGetLastError();
+    }
     const dim3 blk(32, 8, 1);
     if (mixed) k_dinv<float, true><<<stencil_grid(g), blk, 0, st>>>(g, (const float*)vals, diag64, dinv);
     else k_dinv<double, false><<<stencil_grid(g), blk, 0, st>>>(g, (const double*)vals, diag64, dinv);
+    return cudaGetLastError();
+}
+
+static cudaError_t line_apply(const GridGeom& g, const KrylovWork& w, const double* in, double* out, float* hi,
+                              float* lo, cudaStream_t st) {
+    const unsigned nb = (unsigned)(((long long)g.nx * g.ny + kLineThreads - 1) / kLineThreads);
+    k_line_apply<<<nb, kLineThreads, 0, st>>>(g, w.dinv, w.lmul, w.up, in, out, hi, lo, w.S);
     return cudaGetLastError();
 }
 
@@ -366,19 +507,21 @@ cudaError_t krylov_start(const GridGeom& g, long long n, const double* b, double
 }
 
 cudaError_t krylov_iteration(const GridGeom& g, long long n, bool mixed, const void* vals, const double* diag64,
-                             const KrylovWork& w, cudaStream_t st) {
+                             const KrylovWork& w, bool line, cudaStream_t st) {
     const long long nb = krylov_vec_blocks(n);
     const dim3 sg = stencil_grid(g), blk(32, 8, 1);
     const long long ns = (long long)sg.x * sg.y * sg.z;
     k_update_p<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.r, w.v, w.p, w.ph, mixed ? w.phh : nullptr,
-                                                     mixed ? w.phl : nullptr, w.dinv, w.S);
+                                                     mixed ? w.phl : nullptr, line ? nullptr : w.dinv, w.S);
+    if (line) line_apply(g, w, w.p, w.ph, mixed ? w.phh : nullptr, mixed ? w.phl : nullptr, st);
     if (mixed)
         k_spmv_mixed<<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.ph, w.phh, w.phl, w.v, w.rh, w.part, w.S);
     else
         k_spmv<double, false><<<sg, blk, 0, st>>>(g, (const double*)vals, diag64, w.ph, w.v, w.rh, w.part, w.S);
     k_finalize<<<1, kFinThreads, 0, st>>>(w.part, ns, 1, w.S);
     k_update_s<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.r, w.v, w.s, w.sh, mixed ? w.shh : nullptr,
-                                                     mixed ? w.shl : nullptr, w.dinv, w.S);
+                                                     mixed ? w.shl : nullptr, line ? nullptr : w.dinv, w.S);
+    if (line) line_apply(g, w, w.s, w.sh, mixed ? w.shh : nullptr, mixed ? w.shl : nullptr, st);
     if (mixed)
         k_spmv_mixed<<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.sh, w.shh, w.shl, w.t, w.s, w.part, w.S);
     else

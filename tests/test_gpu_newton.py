@@ -45,17 +45,18 @@ def _backward_ok(J, x, b, rtol, tolj):
     return res <= bound, res, bound
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 4, 3), (12, 10, 6), (33, 9, 4)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 4, 3), (12, 10, 6), (33, 9, 4), (7, 3, 19)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("conn", [6, 10])
-def test_linear_solve_matches_oracle(shape, precision, conn):
+@pytest.mark.parametrize("precond", ["zline", "jacobi"])
+def test_linear_solve_matches_oracle(shape, precision, conn, precond):
     prob = _problem(shape, precision, connectivity=conn)
     J, _ = _ref(prob)
     b = synth.cotangent(prob.n, seed=7)
     rtol = 1e-10
     with _grid(prob, precision) as g:
         g.set_state(prob.p, prob.pn)
-        x, st = g.linear_solve(b, rtol=rtol, max_iters=2000)
+        x, st = g.linear_solve(b, rtol=rtol, max_iters=2000, precond=precond)
         x = x.cpu().numpy()
     assert st["converged"] == 1 and st["rel_residual"] <= rtol
     ok, res, bound = _backward_ok(J, x, b, rtol, TOLJ[precision])
@@ -66,6 +67,22 @@ def test_linear_solve_matches_oracle(shape, precision, conn):
         kappa = np.linalg.cond(J.toarray()) if prob.n <= 4000 else 1e8
         err = np.abs(x - x_ref).max() / np.abs(x_ref).max()
         assert err <= 10 * kappa * (rtol + TOLJ["fp64"]), (err, kappa)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_zline_preconditioner_needs_fewer_iterations(precision):
+    """Thin cells (dz = dx / 5) couple vertically 25 times more strongly than
+    horizontally: the z-line preconditioner, exact on those couplings, needs
+    far fewer BiCGStab iterations than the diagonal one."""
+    prob = _problem((24, 20, 32), precision, dt=86400.0, c_r=0.0)
+    b = synth.cotangent(prob.n, seed=12)
+    its = {}
+    with _grid(prob, precision) as g:
+        g.set_state(prob.p, prob.pn)
+        for pc in ("jacobi", "zline"):
+            _, st = g.linear_solve(b, rtol=1e-8, max_iters=5000, precond=pc)
+            its[pc] = st["iterations"]
+    assert its["zline"] * 2 <= its["jacobi"], its
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
