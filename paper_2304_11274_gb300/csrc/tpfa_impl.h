@@ -64,7 +64,7 @@ cudaError_t launch_jvp_fp64(const GridGeom& g, const PhysD& q, bool crk, const A
 cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st);
 cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st);
 
-// Jacobi-preconditioned BiCGStab (tpfa_krylov.cu).  The scalars live on the
+// Preconditioned BiCGStab (tpfa_krylov.cu).  The scalars live on the
 // device; the host polls them.
 struct KrylovScalars {
     double rho, alpha, omega, beta, rr, bb, tol2;

@@ -1,5 +1,5 @@
-// tpfa_krylov.cu -- Jacobi-preconditioned BiCGStab on the assembled Jacobian
-// (the linear solve of a Newton step on Eq. vk), sm_103a.
+// tpfa_krylov.cu -- preconditioned BiCGStab on the assembled Jacobian (the
+// linear solve of a Newton step on Eq. vk), sm_103a.
 //
 // BiCGStab (van der Vorst, 1992) with right preconditioning by M, the
 // tridiagonal part of J along z (default) or its diagonal (Jacobi):
@@ -70,10 +70,8 @@ __device__ __forceinline__ void block_partials(double d0, double d1, double* par
     }
 }
 
-// y = J x over the stencil; partials of (a, y) and (y, y).
-template <typename Real, bool MIXED>
-__global__ void __launch_bounds__(256) k_spmv(GridGeom g, const Real* __restrict__ vals,
-                                              const double* __restrict__ diag64, const double* __restrict__ x,
+// FP64 path: y = J x over the stencil in FP64; partials of (a, y) and (y, y).
+__global__ void __launch_bounds__(256) k_spmv(GridGeom g, const double* __restrict__ vals, const double* __restrict__ x,
                                               double* __restrict__ y, const double* __restrict__ a, double* part,
                                               const KrylovScalars* S) {
     if (S->done) return;  // uniform over the grid
@@ -86,14 +84,13 @@ __global__ void __launch_bounds__(256) k_spmv(GridGeom g, const Real* __restrict
         const int c = i + nx * j + nxy * k;
         const unsigned mask = slot_mask(g, i, j, k);
         const int off[NSLOT] = {-nxy, -nx - 1, -nx, -nx + 1, -1, 0, 1, nx - 1, nx, nx + 1, nxy};
-        const Real* row = vals + row_start(g, i, j, k);
+        const double* row = vals + row_start(g, i, j, k);
         double acc = 0.0;
         int pos = 0;
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) {
             if (!(mask & (1u << s))) continue;
-            const double av = (MIXED && s == SLOT_SELF) ? diag64[c] : as_f64(row[pos]);
-            acc = fma(av, x[c + off[s]], acc);
+            acc = fma(row[pos], x[c + off[s]], acc);
             ++pos;
         }
         y[c] = acc;
@@ -452,12 +449,6 @@ __global__ void __launch_bounds__(kVecThreads) k_add_delta(long long n, Real* p,
         p[c] = (Real)((double)p[c] + d[c]);
 }
 
-// -R into b
-__global__ void __launch_bounds__(kVecThreads) k_negate(long long n, const double* __restrict__ a, double* b) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-        b[c] = -a[c];
-}
-
 dim3 stencil_grid(const GridGeom& g) { return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz); }
 
 }  // namespace
@@ -517,7 +508,7 @@ cudaError_t krylov_iteration(const GridGeom& g, long long n, bool mixed, const v
     if (mixed)
         k_spmv_mixed<<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.ph, w.phh, w.phl, w.v, w.rh, w.part, w.S);
     else
-        k_spmv<double, false><<<sg, blk, 0, st>>>(g, (const double*)vals, diag64, w.ph, w.v, w.rh, w.part, w.S);
+        k_spmv<<<sg, blk, 0, st>>>(g, (const double*)vals, w.ph, w.v, w.rh, w.part, w.S);
     k_finalize<<<1, kFinThreads, 0, st>>>(w.part, ns, 1, w.S);
     k_update_s<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.r, w.v, w.s, w.sh, mixed ? w.shh : nullptr,
                                                      mixed ? w.shl : nullptr, line ? nullptr : w.dinv, w.S);
@@ -525,15 +516,10 @@ cudaError_t krylov_iteration(const GridGeom& g, long long n, bool mixed, const v
     if (mixed)
         k_spmv_mixed<<<sg, blk, 0, st>>>(g, (const float*)vals, diag64, w.sh, w.shh, w.shl, w.t, w.s, w.part, w.S);
     else
-        k_spmv<double, false><<<sg, blk, 0, st>>>(g, (const double*)vals, diag64, w.sh, w.t, w.s, w.part, w.S);
+        k_spmv<<<sg, blk, 0, st>>>(g, (const double*)vals, w.sh, w.t, w.s, w.part, w.S);
     k_finalize<<<1, kFinThreads, 0, st>>>(w.part, ns, 2, w.S);
     k_update_xr<<<(unsigned)nb, kVecThreads, 0, st>>>(n, w.x, w.ph, w.sh, w.s, w.t, w.r, w.rh, w.part, w.S);
     k_finalize<<<1, kFinThreads, 0, st>>>(w.part, nb, 3, w.S);
-    return cudaGetLastError();
-}
-
-cudaError_t krylov_negate(long long n, const double* a, double* b, cudaStream_t st) {
-    k_negate<<<(unsigned)krylov_vec_blocks(n), kVecThreads, 0, st>>>(n, a, b);
     return cudaGetLastError();
 }
 

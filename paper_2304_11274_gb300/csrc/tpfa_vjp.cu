@@ -12,7 +12,7 @@
 // row L's link seen from L; it equals -dF_iL/dp_i except at an exact tie
 // dPhi = 0, where it is evaluated from L's side.  Nothing is stored between
 // the forward assembly and this pass: densities, upwind choices and
-// mobilities are recomputed (gather form, one thread per cell, no atomics).
+// mobilities are recomputed (gather form, no atomics).
 //
 // FP64 path: links, sums and outputs in FP64, one thread per cell.
 //
@@ -26,10 +26,9 @@
 // lo_L) is formed in FP32 (for the two vertical links: in FP64, then
 // narrowed), so each term is accurate relative to itself (a smooth v loses
 // nothing); the terms are FP32 products Kahan-summed in FP32 in slot order
-// and combined in FP64.  Two
-// kernels give identical bits: the y-march of the assembly (its adjoint
-// mode, the production kernel) and a one-thread-per-cell gather with
-// checked loads.
+// and combined in FP64.  Two kernels give identical bits: the y-march of the
+// assembly (its adjoint mode, the production kernel) and a
+// one-thread-per-cell gather with checked loads.
 #include <cuda_runtime.h>
 
 #include "tpfa_impl.h"
@@ -41,7 +40,7 @@ namespace {
 
 // Checked load: an index outside [0, N) or a NULL array latches
 // STATUS_DEVICE_CHECK (reported as TPFA_ERR_DEVICE_CHECK by tpfa_sync_status)
-// and reads nothing.  The adjoint kernel reads every field through it.
+// and reads nothing.  The gather kernels read every field through it.
 template <typename T>
 __device__ __forceinline__ T ld_chk(const T* p, long long idx, long long N, unsigned int* status) {
     if (p == nullptr || idx < 0 || idx >= N) {
