@@ -245,7 +245,7 @@ int tpfa_sync_status(tpfa_handle h, void* stream);
 
 /*
  * Tiling of the assembly kernel: a warp marches along y over
- * `rows_per_march` rows of a 32-cell x-segment, and a block stacks
+ * `rows_per_march` (1 to 64) rows of a 32-cell x-segment, and a block stacks
  * `warps_per_block` (4 or 8) consecutive z-planes.  Results do not depend on
  * the tiling (every row is summed in the same order); only speed does.  The
  * J w and adjoint marches use the same tiling, with the rows per march

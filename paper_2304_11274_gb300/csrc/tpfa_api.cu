@@ -1092,7 +1092,8 @@ std::map<std::string, std::pair<int, int>> cache_read(const char* path) {
     char line[512];
     while (fgets(line, sizeof line, fp)) {
         if (line[0] == '#') continue;
-        if (sscanf(line, "%255s %d %d", key, &jy, &w) == 3 && jy >= 1 && (w == 4 || w == 8)) m[key] = {jy, w};
+        if (sscanf(line, "%255s %d %d", key, &jy, &w) == 3 && jy >= 1 && jy <= 64 && (w == 4 || w == 8))
+            m[key] = {jy, w};
     }
     fclose(fp);
     return m;
@@ -1247,8 +1248,8 @@ extern "C" {
 int tpfa_set_tiling(tpfa_handle h, int rows_per_march, int warps_per_block) {
     int rc = check_handle(h);
     if (rc) return rc;
-    if (rows_per_march < 1 || (warps_per_block != 4 && warps_per_block != 8))
-        return fail(TPFA_ERR_INVALID_ARG, "rows_per_march must be >= 1 and warps_per_block 4 or 8");
+    if (rows_per_march < 1 || rows_per_march > 64 || (warps_per_block != 4 && warps_per_block != 8))
+        return fail(TPFA_ERR_INVALID_ARG, "rows_per_march must be in [1, 64] and warps_per_block 4 or 8");
     h->JY = rows_per_march;
     h->W = warps_per_block;
     return TPFA_OK;

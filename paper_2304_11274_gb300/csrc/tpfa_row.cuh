@@ -123,4 +123,51 @@ __device__ __forceinline__ RowSums assemble_row(const PhysD& q, const CellVal<do
     return out;
 }
 
+// Row (i, j, k) read straight from global memory and written out: the cell
+// and its neighbours, densities recomputed per neighbour as in Algorithm 1.
+// The naive kernel runs it for every cell; the tiled kernel runs it for the
+// rows whose reused links met an exact tie.  A lane with act == false works
+// on cell (0, j, k) with no links and stores nothing, so every address formed
+// stays inside the arrays.
+template <typename Real, bool CRK, bool JAC>
+__device__ __forceinline__ void naive_row(const GridGeom& g, const typename PhysOf<Real>::type& q,
+                                          const AsmFields<Real>& f, const AsmOut<Real>& o, bool act, int i, int j,
+                                          int k) {
+    const long long nx = g.nx, nxy = nx * g.ny;
+    const long long c = (act ? (long long)i + nx * j : 0) + nxy * k;
+    const unsigned mask = act ? slot_mask(g, i, j, k) : (1u << SLOT_SELF);
+    const long long off[NSLOT] = {-nxy, -nx - 1, -nx, -nx + 1, -1, 0, 1, nx - 1, nx, nx + 1, nxy};
+    const CellVal<Real> me = make_cell(q, f.p[c], f.z[c]);
+    CellVal<Real> nb[NSLOT];
+    Real T[NSLOT];
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        nb[s] = me;
+        T[s] = Real(0);
+        const bool valid = s != SLOT_SELF && (mask & (1u << s));
+        const long long d = valid ? c + off[s] : c;  // in range even if a load is hoisted
+        if (valid) nb[s] = make_cell(q, f.p[d], f.z[d]);
+    }
+    if (mask & (1u << 0)) T[0] = f.Tz[(mask & 1u) ? c - nxy : c];
+    if (mask & (1u << 1)) T[1] = f.Tpp[(mask & 2u) ? c - nx - 1 : c];
+    if (mask & (1u << 2)) T[2] = f.Ty[(mask & 4u) ? c - nx : c];
+    if (mask & (1u << 3)) T[3] = f.Tmp[(mask & 8u) ? c - nx + 1 : c];
+    if (mask & (1u << 4)) T[4] = f.Tx[(mask & 16u) ? c - 1 : c];
+    if (mask & (1u << 6)) T[6] = f.Tx[c];
+    if (mask & (1u << 7)) T[7] = f.Tmp[c];
+    if (mask & (1u << 8)) T[8] = f.Ty[c];
+    if (mask & (1u << 9)) T[9] = f.Tpp[c];
+    if (mask & (1u << 10)) T[10] = f.Tz[c];
+    const long long rs = act ? row_start(g, i, j, k) : 0;
+    Real* vals = o.vals;
+    auto sink = [&](int pos, Real v) {
+        if (act) vals[rs + pos] = v;
+    };
+    const RowSums r = assemble_row<CRK, JAC>(q, me, nb, T, mask, f.pn[c], f.mn[c], CRK ? f.phi0[c] : Real(0), sink);
+    if (!act) return;
+    if (o.R) o.R[c] = r.R;
+    if (JAC && o.diag64) o.diag64[c] = r.diag64;
+    if (r.bad) atomicOr(o.status, STATUS_NONFINITE);
+}
+
 }  // namespace tpfa

@@ -340,7 +340,11 @@ struct YMarch {
     }
 
     // The ten links of row j (slot order), and the links from row j into
-    // row j+1 for the next step.
+    // row j+1 for the next step.  With TIEFIX a warp whose reused links into
+    // row j-1 met an exact tie evaluates them from row j's side on the spot;
+    // without it (the assembly) they stay reused and the row is recomputed
+    // after the march (ymarch_tile).
+    template <bool TIEFIX>
     __device__ __forceinline__ void eval_links(const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
                                                const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev,
                                                Real Tpp_prev, Real Tmp_prev, LinkOut<Real> (&S)[NSLOT],
@@ -399,7 +403,7 @@ struct YMarch {
             if (lane == 0) S[1] = E;
             if (lane == 31) S[3] = E;
         }
-        if (__any_sync(0xffffffffu, Uprev.tie)) {
+        if (TIEFIX && __any_sync(0xffffffffu, Uprev.tie)) {
             // an exact tie among row j-1's links: evaluate those links directly
             S[2] = link(q, Ty_prev, C.c, P.c);
             if (DIAG) {
@@ -425,7 +429,7 @@ struct YMarch {
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
-        eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        eval_links<false>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
 
         // offsets of this row's CSR segment and of this lane's row in it
         const int per = 1 + ey + ez, perx = 1 + g.diag * ey;
@@ -466,7 +470,7 @@ struct YMarch {
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
-        eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        eval_links<true>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
         const float ws[NSLOT] = {wzm, wP.m, wP.c, wP.p, wC.m, 0.f, wC.p, wN.m, wN.c, wN.p, wzp};
         Kahan2 ks;
 #pragma unroll
@@ -510,7 +514,7 @@ struct YMarch {
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
-        eval_links(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        eval_links<true>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
         Real Tx_m = vshfl_up(D.Tx), Tl = vshfl_up(Tpp_prev), Tr = vshfl_down(Tmp_prev);
         if (lane == 0) Tx_m = D.hT1, Tl = D.hT2;
         if (lane == 31) Tr = D.hT2;
@@ -707,6 +711,9 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
     YUp<Real> U = M.up_links(P, C, Ty_prev, Tpp_prev, Tmp_prev);
     int s0 = 1, s1 = 2, s2 = 0;  // ring slots of rows j, j+1, j+2
     int rowbase = M.row_base(j0);
+    // rows whose links into the previous row (reused by negation) met an
+    // exact tie dPhi == 0: recomputed after the march (bit j - j0; JY <= 64)
+    unsigned long long tie_rows = 0ull;
 
     for (int j = j0; j < j1; ++j) {
         // row j+2 is requested now and used two steps later; row j+1 arrived
@@ -720,19 +727,23 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
         s2 = st;
         Real* buf = stage + ((j - j0) & 1) * BUF;
         M.buffer_ready();
+        if (__any_sync(0xffffffffu, U.tie)) tie_rows |= 1ull << (j - j0);
         const bool injk = zint && j > 0 && j + 1 < M.ny;
-        if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf, rowbase);
-        else if (injk) U = M.template row<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf, rowbase);
-        else U = M.template row<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, buf, rowbase);
+        const Real t0 = Real(0);  // the reused links are not re-evaluated here
+        if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, t0, t0, t0, buf, rowbase);
+        else if (injk) U = M.template row<1>(j, P, C, N, D, U, t0, t0, t0, buf, rowbase);
+        else U = M.template row<0>(j, P, C, N, D, U, t0, t0, t0, buf, rowbase);
         rowbase += M.row_base_step(j);
-        Ty_prev = D.Ty;
-        Tpp_prev = D.Tpp;
-        Tmp_prev = D.Tmp;
         P = C;
         C = N;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     M.drain();
+    if (tie_rows) {  // warp-uniform; every bulk store of the warp has completed
+        __syncwarp();
+        for (int b = 0; b < 64; ++b)
+            if ((tie_rows >> b) & 1ull) naive_row<Real, CRK, JAC>(g, q, f, o, M.act, M.i, j0 + b, k);
+    }
 }
 
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>

@@ -124,9 +124,12 @@ def test_grid_autotune_keeps_results(tmp_path):
     jy, w = g.autotune(str(tmp_path / "t.txt"))
     assert jy in (16, 32, 64) and w in (4, 8)
     assert _same(before, _single(g))
-    for jy, w in [(7, 4), (1, 8), (200, 4)]:
+    for jy, w in [(7, 4), (1, 8), (64, 4)]:
         g.set_tiling(jy, w)
         assert _same(before, _single(g))
+    from paper_2304_11274_gb300.api import TPFAError
+    with pytest.raises(TPFAError):
+        g.set_tiling(65, 4)  # a march longer than 64 rows is rejected
     g.close()
 
 
