@@ -5,7 +5,9 @@
 //   (J w)_K = dA_K/dp_K w_K + sum_{L in adj(K)} ( dF_KL/dp_K w_K + dF_KL/dp_L w_L )
 // without storing J: the operator a Krylov solver of Eq. vk needs.  The same
 // pass can also produce R_K, summed exactly as the assembly kernels sum it,
-// so R here is bit-identical to tpfa_assemble_residual's.
+// so R here is bit-identical to tpfa_assemble_residual's.  As in the
+// assembly, the tiled kernel reuses the links into the previous y-row and
+// recomputes, after its march, the rows where one of them was an exact tie.
 //
 // Mixed path: w is narrowed to FP32 (truncation, on the integer pipe); per
 // link the term dF/dp_K w_K + dF/dp_L w_L is one FP32 fma of the link's FP32
@@ -52,14 +54,13 @@ __device__ __forceinline__ const Real* slot_T(const AsmFields<Real>& f, int s, i
     }
 }
 
+// J w (and R) of cell (i, j, k) from global memory: the naive kernel's row,
+// and the tiled kernel's for the rows whose reused links met an exact tie.
 template <typename Real, bool CRK>
-__global__ void __launch_bounds__(256) k_jvp(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f,
-                                             const double* __restrict__ w, double* __restrict__ Jw,
-                                             double* __restrict__ R, unsigned int* status) {
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
+__device__ __forceinline__ void jvp_row(const GridGeom& g, const typename PhysOf<Real>::type& q,
+                                        const AsmFields<Real>& f, const double* __restrict__ w,
+                                        double* __restrict__ Jw, double* __restrict__ R, unsigned int* status, int i,
+                                        int j, int k) {
     const int nx = g.nx, nxy = nx * g.ny;
     const long long NN = (long long)nxy * g.nz;
     const int c = i + nx * j + nxy * k;
@@ -109,6 +110,15 @@ __global__ void __launch_bounds__(256) k_jvp(GridGeom g, typename PhysOf<Real>::
     Jw[c] = jw;
     if (R) R[c] = r;
     if (nonfinite(jw) || (R && nonfinite(r))) atomicOr(status, STATUS_NONFINITE);
+}
+
+template <typename Real, bool CRK>
+__global__ void __launch_bounds__(256) k_jvp(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f,
+                                             const double* __restrict__ w, double* __restrict__ Jw,
+                                             double* __restrict__ R, unsigned int* status) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    if (i < g.nx && j < g.ny) jvp_row<Real, CRK>(g, q, f, w, Jw, R, status, i, j, blockIdx.z);
 }
 
 // ---------------------------------------------------------------- y-march J w (mixed)
@@ -161,10 +171,12 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
     }
     YUp<float> U = M.up_links(P, C, Ty_prev, Tpp_prev, Tmp_prev);
     int s0 = 1, s1 = 2, s2 = 0;  // ring slots of rows j, j+1, j+2
+    unsigned long long tie_rows = 0ull;  // rows recomputed after the march (as in the assembly)
 
     for (int j = j0; j < j1; ++j) {
         M.issue_row(j + 2, s2);
         M.wait_all_but_newest();
+        if (__any_sync(0xffffffffu, U.tie)) tie_rows |= 1ull << (j - j0);
         const YRow<float> N = M.row_cells(s1);
         const YW wN = M.w_row(s1);
         const YIn<float> D = M.read_in(s0);
@@ -175,21 +187,23 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         s1 = s2;
         s2 = st;
         const bool injk = zint && j > 0 && j + 1 < M.ny;
+        const float t0 = 0.f;  // the reused links are not re-evaluated in the march
         if (injk && M.xint)
-            U = M.template row_jvp<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp);
+            U = M.template row_jvp<2>(j, P, C, N, D, U, t0, t0, t0, wP, wC, wN, wzm, wzp);
         else if (injk)
-            U = M.template row_jvp<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp);
+            U = M.template row_jvp<1>(j, P, C, N, D, U, t0, t0, t0, wP, wC, wN, wzm, wzp);
         else
-            U = M.template row_jvp<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, wP, wC, wN, wzm, wzp);
-        Ty_prev = D.Ty;
-        Tpp_prev = D.Tpp;
-        Tmp_prev = D.Tmp;
+            U = M.template row_jvp<0>(j, P, C, N, D, U, t0, t0, t0, wP, wC, wN, wzm, wzp);
         P = C;
         C = N;
         wP = wC;
         wC = wN;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (tie_rows) {  // warp-uniform
+        for (int b = 0; b < 64; ++b)
+            if (((tie_rows >> b) & 1ull) && M.act) jvp_row<float, CRK>(g, q, f, w, Jw, o.R, o.status, M.i, j0 + b, k);
+    }
 }
 
 template <bool DIAG, bool CRK, int W>

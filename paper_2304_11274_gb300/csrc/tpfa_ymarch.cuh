@@ -341,9 +341,9 @@ struct YMarch {
 
     // The ten links of row j (slot order), and the links from row j into
     // row j+1 for the next step.  With TIEFIX a warp whose reused links into
-    // row j-1 met an exact tie evaluates them from row j's side on the spot;
-    // without it (the assembly) they stay reused and the row is recomputed
-    // after the march (ymarch_tile).
+    // row j-1 met an exact tie evaluates them from row j's side on the spot
+    // (the adjoint); without it (the assembly and J w) they stay reused and
+    // the row is recomputed after the march.
     template <bool TIEFIX>
     __device__ __forceinline__ void eval_links(const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
                                                const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev,
@@ -470,7 +470,7 @@ struct YMarch {
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
-        eval_links<true>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        eval_links<false>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
         const float ws[NSLOT] = {wzm, wP.m, wP.c, wP.p, wC.m, 0.f, wC.p, wN.m, wN.c, wN.p, wzp};
         Kahan2 ks;
 #pragma unroll

@@ -16,6 +16,7 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+from paper_2304_11274_gb300 import synth
 
 EPS32 = 2.0 ** -24
 EPS64 = 2.0 ** -53
@@ -107,3 +108,33 @@ def subgrid_row(prob, i, j, k):
         Jrow[g] = out["J"][e]
         dphi[g] = out["dphi"][e]
     return out["R"][li], Jrow, dphi
+
+
+def tie_sweep_problem(precision, conn=10):
+    """Exact ties dPhi == 0 on links the tiled kernel reuses from the previous
+    y-row: row j = 0 at p = p_ref = 0 (rho = rho_ref exactly) and depth 1 m,
+    row j = 1 at depth 3 m with g = 0.5 (so g dz = -1 exactly and dPhi =
+    rho_avg - p_1), its pressures sweeping 4096 consecutive representable
+    values around the root of p_1 = rho_avg(p_1).  Over the sweep rho_avg
+    stays one representable value (c_f = 1e-6 moves it by far less than an
+    ulp), so exactly one p_1 of the sweep equals it: there the y-link and
+    both diagonal links into that cell are exact ties, in either precision."""
+    dt = np.float32 if precision == "mixed" else np.float64
+    nx, ny, nz = 4096, 2, 1
+    phys = synth.physics(connectivity=conn, p_ref=0.0, c_f=1e-6, g=0.5, c_r=0.0)
+    r = dt(1000.0)
+    for _ in range(60):  # fixed point p = (rho_ref + rho(p)) / 2 in the path's precision
+        r = dt(0.5) * (dt(1000.0) + dt(1000.0) * dt(np.exp(dt(1e-6) * r)))
+    sweep = [r]
+    lo = hi = r
+    for _ in range(nx // 2):
+        lo = np.nextafter(lo, dt(-np.inf))
+        hi = np.nextafter(hi, dt(np.inf))
+        sweep = [lo] + sweep + [hi]
+    p1 = np.array(sweep[:nx], dtype=np.float64)
+    p = np.concatenate([np.zeros(nx), p1])
+    depth = np.concatenate([np.full(nx, 1.0), np.full(nx, 3.0)])
+    rng = np.random.default_rng(9)
+    perm = np.full(nx * ny * nz, 1e-13)
+    poro = rng.uniform(0.1, 0.3, nx * ny * nz)
+    return synth.Problem(nx, ny, nz, phys, perm, poro, depth, p, p.copy())

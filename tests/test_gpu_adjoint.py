@@ -187,3 +187,18 @@ def test_autograd_mixed_matches_oracle_gradient():
         assert _normwise(lk.grad.cpu().numpy(), g_lnk_ref) <= 1e-6
         # p.grad is returned in p's dtype (FP32)
         assert _normwise(p.grad.double().cpu().numpy(), g_p_ref) <= 1e-6
+
+
+@pytest.mark.parametrize("conn", [6, 10])
+def test_vjp_reused_link_ties(conn):
+    """Exact ties on the links the adjoint march reuses from the previous
+    y-row (where dF_Li/dp_i != -dF_iL/dp_i): march and naive gather agree bit
+    for bit."""
+    prob = C.tie_sweep_problem("mixed", conn)
+    v = synth.cotangent(prob.n, seed=22)
+    with _grid(prob, "mixed") as g:
+        g.set_state(prob.p, prob.pn)
+        a = g.vjp(v, kernel="naive")
+        b = g.vjp(v, kernel="tiled")
+        g.sync_status()
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])

@@ -193,3 +193,17 @@ def test_jvp_full_size_sampled():
         worst = max(worst, abs(got[n] - ref) / scale)
     assert worst <= TOL["mixed"], worst
     assert skipped <= len(cells) // 100
+
+
+@pytest.mark.parametrize("conn", [6, 10])
+def test_jvp_reused_link_ties_are_fixed_up(conn):
+    """Exact ties on the links the J w march reuses from the previous y-row:
+    the march recomputes those rows and matches the naive kernel bit for bit."""
+    prob = C.tie_sweep_problem("mixed", conn)
+    w = synth.cotangent(prob.n, seed=21)
+    with _grid(prob, "mixed") as g:
+        g.set_state(prob.p, prob.pn)
+        Jn, Rn = g.jvp(w, want_residual=True, kernel="naive")
+        Jt, Rt = g.jvp(w, want_residual=True, kernel="tiled")
+        g.sync_status()
+        assert torch.equal(Jn, Jt) and torch.equal(Rn, Rt)
