@@ -187,13 +187,9 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         s1 = s2;
         s2 = st;
         const bool injk = zint && j > 0 && j + 1 < M.ny;
-        const float t0 = 0.f;  // the reused links are not re-evaluated in the march
-        if (injk && M.xint)
-            U = M.template row_jvp<2>(j, P, C, N, D, U, t0, t0, t0, wP, wC, wN, wzm, wzp);
-        else if (injk)
-            U = M.template row_jvp<1>(j, P, C, N, D, U, t0, t0, t0, wP, wC, wN, wzm, wzp);
-        else
-            U = M.template row_jvp<0>(j, P, C, N, D, U, t0, t0, t0, wP, wC, wN, wzm, wzp);
+        if (injk && M.xint) U = M.template row_jvp<2>(j, P, C, N, D, U, wP, wC, wN, wzm, wzp);
+        else if (injk) U = M.template row_jvp<1>(j, P, C, N, D, U, wP, wC, wN, wzm, wzp);
+        else U = M.template row_jvp<0>(j, P, C, N, D, U, wP, wC, wN, wzm, wzp);
         P = C;
         C = N;
         wP = wC;

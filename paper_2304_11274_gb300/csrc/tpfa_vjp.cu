@@ -138,16 +138,14 @@ __device__ __forceinline__ float geo_of(const LinkGeo& lg, int s) {
     }
 }
 
-// The mixed path's adjoint, one thread per cell (the march's twin).
+// The mixed path's adjoint of cell (i, j, k) from global memory: the naive
+// kernel's row, and the tiled kernel's for the rows where a link had zero
+// flux (every exact tie).
 template <bool CRK>
-__global__ void __launch_bounds__(256) k_vjp_mixed(GridGeom g, PhysF q, AsmFields<float> f,
-                                                   const float* __restrict__ kperm, LinkGeo lg,
-                                                   const double* __restrict__ v, double* __restrict__ g_p,
-                                                   double* __restrict__ g_lnk, unsigned int* status) {
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
+__device__ __forceinline__ void vjp_row(const GridGeom& g, const PhysF& q, const AsmFields<float>& f,
+                                        const float* __restrict__ kperm, const LinkGeo& lg,
+                                        const double* __restrict__ v, double* __restrict__ g_p,
+                                        double* __restrict__ g_lnk, unsigned int* status, int i, int j, int k) {
     const int nx = g.nx, nxy = nx * g.ny;
     const int c = i + nx * j + nxy * k;
     const long long NN = (long long)nxy * g.nz;
@@ -199,6 +197,16 @@ __global__ void __launch_bounds__(256) k_vjp_mixed(GridGeom g, PhysF q, AsmField
     g_p[c] = gp;
     if (g_lnk) g_lnk[c] = gk;
     if (nonfinite(gp) || nonfinite(gk)) atomicOr(status, STATUS_NONFINITE);
+}
+
+template <bool CRK>
+__global__ void __launch_bounds__(256) k_vjp_mixed(GridGeom g, PhysF q, AsmFields<float> f,
+                                                   const float* __restrict__ kperm, LinkGeo lg,
+                                                   const double* __restrict__ v, double* __restrict__ g_p,
+                                                   double* __restrict__ g_lnk, unsigned int* status) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    if (i < g.nx && j < g.ny) vjp_row<CRK>(g, q, f, kperm, lg, v, g_p, g_lnk, status, i, j, blockIdx.z);
 }
 
 // ---------------------------------------------------------------- y-march adjoint (mixed)
@@ -254,6 +262,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
     }
     YUp<float> U = M.up_links(P, C, Ty_prev, Tpp_prev, Tmp_prev);
     int s0 = 1, s1 = 2, s2 = 0;  // ring slots of rows j, j+1, j+2
+    unsigned long long fix_rows = 0ull;  // rows with a zero flux, recomputed after the march
 
     for (int j = j0; j < j1; ++j) {
         M.issue_row(j + 2, s2);
@@ -269,12 +278,14 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         s1 = s2;
         s2 = st;
         const bool injk = zint && j > 0 && j + 1 < M.ny;
+        bool fix;
         if (injk && M.xint)
-            U = M.template row_vjp<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC);
+            U = M.template row_vjp<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC, fix);
         else if (injk)
-            U = M.template row_vjp<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC);
+            U = M.template row_vjp<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC, fix);
         else
-            U = M.template row_vjp<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC);
+            U = M.template row_vjp<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC, fix);
+        if (fix) fix_rows |= 1ull << (j - j0);
         Ty_prev = D.Ty;
         Tpp_prev = D.Tpp;
         Tmp_prev = D.Tmp;
@@ -284,6 +295,11 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         vC = vN;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (fix_rows) {  // warp-uniform
+        for (int b = 0; b < 64; ++b)
+            if (((fix_rows >> b) & 1ull) && M.act)
+                vjp_row<CRK>(g, q, f, kperm, lg, v, g_p, g_lnk, o.status, M.i, j0 + b, k);
+    }
 }
 
 template <bool DIAG, bool CRK, int W>

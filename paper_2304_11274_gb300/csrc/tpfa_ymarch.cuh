@@ -340,15 +340,13 @@ struct YMarch {
     }
 
     // The ten links of row j (slot order), and the links from row j into
-    // row j+1 for the next step.  With TIEFIX a warp whose reused links into
-    // row j-1 met an exact tie evaluates them from row j's side on the spot
-    // (the adjoint); without it (the assembly and J w) they stay reused and
-    // the row is recomputed after the march.
-    template <bool TIEFIX>
+    // row j+1 for the next step.  The links into row j-1 are the negations of
+    // the previous step's, exact except at a tie dPhi == 0 (where each end
+    // takes the other cell as upstream): U.tie flags those, and the marches
+    // recompute the affected rows afterwards.
     __device__ __forceinline__ void eval_links(const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
-                                               const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev,
-                                               Real Tpp_prev, Real Tmp_prev, LinkOut<Real> (&S)[NSLOT],
-                                               YUp<Real>& U) const {
+                                               const YIn<Real>& D, const YUp<Real>& Uprev,
+                                               LinkOut<Real> (&S)[NSLOT], YUp<Real>& U) const {
         Real Tx_m = vshfl_up(D.Tx);
         if (lane == 0) Tx_m = D.hT1;
         const CellVal<Real> zmc = make_cell(q, D.p_zm, D.z_zm);
@@ -403,17 +401,6 @@ struct YMarch {
             if (lane == 0) S[1] = E;
             if (lane == 31) S[3] = E;
         }
-        if (TIEFIX && __any_sync(0xffffffffu, Uprev.tie)) {
-            // an exact tie among row j-1's links: evaluate those links directly
-            S[2] = link(q, Ty_prev, C.c, P.c);
-            if (DIAG) {
-                Real Tl = vshfl_up(Tpp_prev), Tr = vshfl_down(Tmp_prev);
-                if (lane == 0) Tl = D.hT2;
-                if (lane == 31) Tr = D.hT2;
-                S[1] = link(q, Tl, C.c, P.m);
-                S[3] = link(q, Tr, C.c, P.p);
-            }
-        }
     }
 
     // Assemble row j.  P, C, N: rows j-1, j, j+1.  Uprev: links from row j-1
@@ -421,15 +408,15 @@ struct YMarch {
     // row j into row j+1.
     template <int PATH>
     __device__ __forceinline__ YUp<Real> row(int j, const YRow<Real>& P, const YRow<Real>& C, const YRow<Real>& N,
-                                             const YIn<Real>& D, const YUp<Real>& Uprev, Real Ty_prev, Real Tpp_prev,
-                                             Real Tmp_prev, Real* buf, int rowbase) const {
+                                             const YIn<Real>& D, const YUp<Real>& Uprev, Real* buf,
+                                             int rowbase) const {
         constexpr bool FULL = PATH == 2, INJK = PATH >= 1;
         constexpr int L = DIAG ? 11 : 7, LX = DIAG ? 3 : 1;  // interior row length; x links per side
         const int ey = INJK ? 2 : axis_links(j, ny);
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
-        eval_links<false>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        eval_links(P, C, N, D, Uprev, S, U);
 
         // offsets of this row's CSR segment and of this lane's row in it
         const int per = 1 + ey + ez, perx = 1 + g.diag * ey;
@@ -465,12 +452,12 @@ struct YMarch {
     template <int PATH>
     __device__ __forceinline__ YUp<Real> row_jvp(int j, const YRow<Real>& P, const YRow<Real>& C,
                                                  const YRow<Real>& N, const YIn<Real>& D, const YUp<Real>& Uprev,
-                                                 Real Ty_prev, Real Tpp_prev, Real Tmp_prev, const YW& wP,
-                                                 const YW& wC, const YW& wN, float wzm, float wzp) const {
+                                                 const YW& wP, const YW& wC, const YW& wN, float wzm,
+                                                 float wzp) const {
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
-        eval_links<false>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        eval_links(P, C, N, D, Uprev, S, U);
         const float ws[NSLOT] = {wzm, wP.m, wP.c, wP.p, wC.m, 0.f, wC.p, wN.m, wN.c, wN.p, wzp};
         Kahan2 ks;
 #pragma unroll
@@ -502,19 +489,20 @@ struct YMarch {
     // the vertical links), the terms dF_KL/dp_K dv and F_KL (k_L / (k_K +
     // k_L)) dv share one FP32x2 Kahan sum in slot order; k_L / (k_K + k_L) =
     // Upsilon_KL (d/A) / (2 k_K) for the harmonic two-point transmissibility.
-    // A warp that meets a link with F == 0 (every exact tie) adds, for each
-    // link, v_L (dF_KL/dp_K + dF_LK/dp_K) with the second derivative
-    // evaluated from L's side (zero except at a tie).
+    // The links into row j-1 are reused by negation, which is exact except
+    // at a tie; a tie has zero flux, so `fix` reports (warp-uniformly) a row
+    // where any link had F == 0, and the caller recomputes it after the march
+    // with the full formulation (which adds the tie terms).
     template <int PATH>
     __device__ __forceinline__ YUp<Real> row_vjp(int j, const YRow<Real>& P, const YRow<Real>& C,
                                                  const YRow<Real>& N, const YIn<Real>& D, const YUp<Real>& Uprev,
                                                  Real Ty_prev, Real Tpp_prev, Real Tmp_prev, const YV& vP,
                                                  const YV& vC, const YV& vN, double vd, double vzm, double vzp,
-                                                 float kC) const {
+                                                 float kC, bool& fix) const {
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
         YUp<Real> U;
-        eval_links<true>(P, C, N, D, Uprev, Ty_prev, Tpp_prev, Tmp_prev, S, U);
+        eval_links(P, C, N, D, Uprev, S, U);
         Real Tx_m = vshfl_up(D.Tx), Tl = vshfl_up(Tpp_prev), Tr = vshfl_down(Tmp_prev);
         if (lane == 0) Tx_m = D.hT1, Tl = D.hT2;
         if (lane == 31) Tr = D.hT2;
@@ -535,26 +523,12 @@ struct YMarch {
             ks.add(f2(__fmul_rn(S[s].Da, dv), __fmul_rn(__fmul_rn(S[s].F, ratio), dv)));
             zero_flux |= S[s].F == 0.f;
         }
-        double corr = 0.0;
-        if (__any_sync(0xffffffffu, zero_flux)) {
-            const CellVal<Real> zmc = make_cell(q, D.p_zm, D.z_zm);
-            const CellVal<Real> zpc = make_cell(q, D.p_zp, D.z_zp);
-            const CellVal<Real> nb[NSLOT] = {zmc, P.m, P.c, P.p, C.m, C.c, C.p, N.m, N.c, N.p, zpc};
-#pragma unroll
-            for (int s = 0; s < NSLOT; ++s) {
-                if (s == SLOT_SELF || !(mask & (1u << s))) continue;
-                const float dLK = link(q, Ts[s], nb[s], C.c).Db;
-                const double vL = s == 0    ? vzm
-                                  : s == 10 ? vzp
-                                            : __dadd_rn(widen(vs[s].hi), widen(vs[s].lo));
-                corr = __fma_rn(vL, widen(__fadd_rn(S[s].Da, dLK)), corr);
-            }
-        }
+        fix = __any_sync(0xffffffffu, zero_flux);
         const AccF acc = accumulation<CRK>(q, C.c.p, D.pn, D.mn, C.c.rho, D.phi0);
         if (act) {
             const int c = kb + nx * j + i;
             const double gp =
-                __dadd_rn(__fma_rn(vd, widen(acc.dA), __dadd_rn(widen(ks.s.x), -widen(ks.c.x))), corr);
+                __dadd_rn(__fma_rn(vd, widen(acc.dA), __dadd_rn(widen(ks.s.x), -widen(ks.c.x))), 0.0);
             const double gk = __dadd_rn(widen(ks.s.y), -widen(ks.c.y));
             gP[c] = gp;
             if (gK) gK[c] = gk;
@@ -729,10 +703,9 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
         M.buffer_ready();
         if (__any_sync(0xffffffffu, U.tie)) tie_rows |= 1ull << (j - j0);
         const bool injk = zint && j > 0 && j + 1 < M.ny;
-        const Real t0 = Real(0);  // the reused links are not re-evaluated here
-        if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, t0, t0, t0, buf, rowbase);
-        else if (injk) U = M.template row<1>(j, P, C, N, D, U, t0, t0, t0, buf, rowbase);
-        else U = M.template row<0>(j, P, C, N, D, U, t0, t0, t0, buf, rowbase);
+        if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, buf, rowbase);
+        else if (injk) U = M.template row<1>(j, P, C, N, D, U, buf, rowbase);
+        else U = M.template row<0>(j, P, C, N, D, U, buf, rowbase);
         rowbase += M.row_base_step(j);
         P = C;
         C = N;

@@ -165,5 +165,30 @@ def test_uneven_64_model_ensemble_bit_identical():
         for m, g in enumerate(grids):
             assert _same(outs[m], _single(g)), m
             g.sync_status()
+        # sampled rows of four models against the oracle (each row on its
+        # clipped 3 x 3 x 3 box); the residual bar is normwise over the
+        # sample, the Jacobian bar row-wise
+        rng = np.random.default_rng(31)
+        for m in (0, 17, 40, 63):
+            prob, g = probs[m], grids[m]
+            R, vals, diag = (x.cpu().numpy() for x in outs[m])
+            rp, ci = (x.cpu().numpy() for x in g.pattern())
+            worst_R, scale_R = 0.0, 0.0
+            for _ in range(100):
+                i, j, k = (int(rng.integers(n)) for n in (prob.nx, prob.ny, prob.nz))
+                c = i + prob.nx * (j + prob.ny * k)
+                R_ref, Jrow, dphi = C.subgrid_row(prob, i, j, k)
+                worst_R = max(worst_R, abs(R[c] - R_ref))
+                scale_R = max(scale_R, abs(R_ref))
+                cols = ci[rp[c]:rp[c + 1]]
+                assert sorted(Jrow) == list(cols)
+                if any(abs(dphi[L]) <= 32 * C.EPS32 * (abs(prob.p[c] - prob.p[L]) + 1.1e4 * abs(prob.depth[c] - prob.depth[L]))
+                       for L in Jrow if L != c):
+                    continue
+                row = vals[rp[c]:rp[c + 1]].astype(np.float64)
+                row[list(cols).index(c)] = diag[c]
+                ref = np.array([Jrow[L] for L in cols])
+                assert np.abs(row - ref).max() <= 1e-6 * np.abs(ref).max(), (m, i, j, k)
+            assert worst_R <= 1e-6 * scale_R, (m, worst_R, scale_R)
     for g in grids:
         g.close()
