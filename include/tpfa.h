@@ -71,10 +71,19 @@ typedef enum {
     TPFA_KERNEL_AUTO = 0,  /* the library's choice (currently TILED) */
     TPFA_KERNEL_NAIVE = 1, /* one thread per cell, every neighbour read from
                               global memory: the correctness baseline */
-    TPFA_KERNEL_TILED = 2  /* a warp per 32-cell x-segment of a z-plane,
+    TPFA_KERNEL_TILED = 2, /* a warp per 32-cell x-segment of a z-plane,
                               marching along y with rows j-1, j, j+1 held in
                               registers and x-neighbours exchanged by warp
-                              shuffles */
+                              shuffles; each lane prefetches its row inputs
+                              with cp.async */
+    TPFA_KERNEL_TILED_TMA = 3 /* TILED with 4 warps per block on 4
+                              consecutive x-segments of one plane, each row's
+                              inputs fetched for the whole block as a few
+                              boxes by the tensor memory accelerator
+                              (cp.async.bulk.tensor) into a shared ring;
+                              assembly calls only, TPFA_MIXED, nx a multiple
+                              of 4 and p, p^n 16-byte aligned, else
+                              TPFA_ERR_INVALID_ARG */
 } tpfa_kernel;
 
 typedef struct {
@@ -235,9 +244,10 @@ int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* str
 
 /*
  * Wait for `stream`, then report and clear device-side errors latched since
- * the last call: TPFA_ERR_DEVICE_CHECK if a checked device access was out of
- * range (and skipped), else TPFA_ERR_NONFINITE if any assembled value was
- * NaN/Inf.
+ * the last call: TPFA_ERR_TIMEOUT if a bounded device-side wait ran out (the
+ * TMA march's row waits; that launch's outputs are incomplete), else
+ * TPFA_ERR_DEVICE_CHECK if a checked device access was out of range (and
+ * skipped), else TPFA_ERR_NONFINITE if any assembled value was NaN/Inf.
  */
 int tpfa_sync_status(tpfa_handle h, void* stream);
 

@@ -105,6 +105,14 @@ struct tpfa_grid {
     int JY = 32;  // rows per warp march (tpfa_autotune may change it)
     int sms = 0;  // multiprocessors of the grid's device
     int W = 4;    // warps (z-planes) per block
+    // tensor maps of the TMA march (mixed path): the library-owned fields'
+    // maps are encoded once (tm_static: 0 not yet, 1 done, -1 impossible),
+    // those of p and p^n whenever the bound pointers change
+    TmaMaps tm{};
+    int tm_static = 0;
+    bool tm_state = false;
+    const void* tm_p = nullptr;
+    const void* tm_pn = nullptr;
     // buffers of the host-memory entry point, allocated on first use
     void* h_p = nullptr;
     double* h_R = nullptr;
@@ -194,12 +202,41 @@ AsmFields<Real> fields_of(const tpfa_grid* h) {
     return f;
 }
 
+// Whether the TMA march can run at the bound state (mixed path, nx a
+// multiple of 4, every field 16-byte aligned); encodes the tensor maps it
+// needs.
+bool tma_ready(tpfa_grid* h) {
+    if (h->prec != TPFA_MIXED || !h->has_state) return false;
+    if (h->tm_static == 0) h->tm_static = tma_encode_static(&h->tm, h->geom, fields_of<float>(h), h->crk) ? 1 : -1;
+    if (h->tm_static < 0) return false;
+    if (h->tm_p != h->p || h->tm_pn != h->pn) {
+        h->tm_state = tma_encode_state(&h->tm, h->geom, static_cast<const float*>(h->p),
+                                       static_cast<const float*>(h->pn));
+        h->tm_p = h->p;
+        h->tm_pn = h->pn;
+    }
+    return h->tm_state;
+}
+
+// The library's choice of assembly kernel: the per-lane march.  (The TMA
+// march gives the same bits but measured 8 % slower on the 512 x 512 x 256
+// workload: its row waits stall where the per-lane prefetch does not, and
+// it saves no instructions.)
+AsmKernel auto_kernel(tpfa_grid*) { return AsmKernel::YMarch; }
+
 int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st, int k0 = 0,
            int k1 = -1) {
     cudaError_t e;
+    if (kern == AsmKernel::YMarchTma && !tma_ready(h))
+        return fail(TPFA_ERR_INVALID_ARG,
+                    "the TMA march needs the mixed path, nx a multiple of 4 and 16-byte aligned p and p^n");
     if (h->prec == TPFA_MIXED) {
         AsmOut<float> o{R, static_cast<float*>(vals), diag64, h->status};
-        e = launch_assemble_mixed(kern, h->geom, h->qf, h->crk, fields_of<float>(h), o, h->JY, h->W, st, k0, k1);
+        if (kern == AsmKernel::YMarchTma)
+            e = launch_assemble_mixed_tma(h->geom, h->qf, h->crk, fields_of<float>(h), o, h->tm, h->JY, h->W, st, k0,
+                                          k1);
+        else
+            e = launch_assemble_mixed(kern, h->geom, h->qf, h->crk, fields_of<float>(h), o, h->JY, h->W, st, k0, k1);
     } else {
         AsmOut<double> o{R, static_cast<double*>(vals), nullptr, h->status};
         e = launch_assemble_fp64(kern, h->geom, h->qd, h->crk, fields_of<double>(h), o, h->JY, h->W, st, k0, k1);
@@ -552,7 +589,7 @@ int tpfa_assemble_residual(tpfa_handle h, double* R_dev, void* stream) {
     if (!R_dev) return fail(TPFA_ERR_INVALID_ARG, "R must be non-NULL");
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
     DeviceGuard dg(h->device);
-    return launch(h, AsmKernel::YMarch, R_dev, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+    return launch(h, auto_kernel(h), R_dev, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 int tpfa_assemble_jacobian_kernel(tpfa_handle h, tpfa_kernel kern, double* R_dev, void* vals_dev,
@@ -564,8 +601,9 @@ int tpfa_assemble_jacobian_kernel(tpfa_handle h, tpfa_kernel kern, double* R_dev
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
     AsmKernel k;
     switch (kern) {
-        case TPFA_KERNEL_AUTO:
+        case TPFA_KERNEL_AUTO: k = auto_kernel(h); break;
         case TPFA_KERNEL_TILED: k = AsmKernel::YMarch; break;
+        case TPFA_KERNEL_TILED_TMA: k = AsmKernel::YMarchTma; break;
         case TPFA_KERNEL_NAIVE: k = AsmKernel::Naive; break;
         default: return fail(TPFA_ERR_INVALID_ARG, "bad kernel variant %d", (int)kern);
     }
@@ -636,7 +674,7 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
         if (e == cudaSuccess) e = cudaEventRecord(ev_up[s], h->h_up);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_up[s], 0);
         if (e != cudaSuccess) break;
-        rc = launch(h, AsmKernel::YMarch, h->h_R, h->h_vals, h->prec == TPFA_MIXED ? h->h_diag : nullptr, st, k0, k1);
+        rc = launch(h, auto_kernel(h), h->h_R, h->h_vals, h->prec == TPFA_MIXED ? h->h_diag : nullptr, st, k0, k1);
         if (rc) break;
         e = cudaEventRecord(ev_cmp[s], st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->h_down, ev_cmp[s], 0);
@@ -753,7 +791,7 @@ int tpfa_linear_solve(tpfa_handle h, const double* b_dev, double* x_dev, const t
     rc = krylov_workspace(h);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    rc = launch(h, AsmKernel::YMarch, nullptr, h->kv_vals, h->prec == TPFA_MIXED ? h->kv_diag : nullptr, st);
+    rc = launch(h, auto_kernel(h), nullptr, h->kv_vals, h->prec == TPFA_MIXED ? h->kv_diag : nullptr, st);
     if (rc) return rc;
     return krylov_solve(h, b_dev, 1.0, x_dev, opts, stats, st);
 }
@@ -771,7 +809,7 @@ int tpfa_newton_step(tpfa_handle h, void* p_dev, const tpfa_krylov_opts* opts, t
     h->p = p_dev;
     double* R = R_dev ? R_dev : h->kv_R;
     double* x = delta_dev ? delta_dev : h->kv_vec[0];
-    rc = launch(h, AsmKernel::YMarch, R, h->kv_vals, h->prec == TPFA_MIXED ? h->kv_diag : nullptr, st);
+    rc = launch(h, auto_kernel(h), R, h->kv_vals, h->prec == TPFA_MIXED ? h->kv_diag : nullptr, st);
     if (rc) return rc;
     rc = krylov_solve(h, R, -1.0, x, opts, stats, st);
     if (rc) return rc;
@@ -867,6 +905,7 @@ int tpfa_sync_status(tpfa_handle h, void* stream) {
     if (e == cudaSuccess) e = cudaMemcpy(&s, h->status, sizeof s, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && s) e = cudaMemset(h->status, 0, sizeof(unsigned int));
     if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (s & STATUS_TIMEOUT) return fail(TPFA_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (s & STATUS_DEVICE_CHECK) return fail(TPFA_ERR_DEVICE_CHECK, "a device-side bounds check failed");
     if (s & STATUS_NONFINITE) return fail(TPFA_ERR_NONFINITE, "a residual or Jacobian value was NaN or Inf");
     return TPFA_OK;
@@ -1293,10 +1332,10 @@ int tpfa_autotune(tpfa_handle h, const char* cache_path, void* stream) {
             if (e != cudaSuccess) break;
             h->JY = jy;
             h->W = w;
-            for (int r = 0; r < 2 && !rc; ++r) rc = launch(h, AsmKernel::YMarch, (double*)R, vals, (double*)diag, st);
+            for (int r = 0; r < 2 && !rc; ++r) rc = launch(h, auto_kernel(h), (double*)R, vals, (double*)diag, st);
             if (rc) break;
             cudaEventRecord(a, st);
-            for (int r = 0; r < 3 && !rc; ++r) rc = launch(h, AsmKernel::YMarch, (double*)R, vals, (double*)diag, st);
+            for (int r = 0; r < 3 && !rc; ++r) rc = launch(h, auto_kernel(h), (double*)R, vals, (double*)diag, st);
             cudaEventRecord(b, st);
             e = cudaEventSynchronize(b);
             float ms = 0.f;

@@ -12,7 +12,13 @@
 //                        with a register window of three rows, reuse of the
 //                        links into the previous row and staged 16-byte CSR
 //                        stores.
+//   k_assemble_ymarch_tma -- the same march with its row inputs delivered by
+//                        TMA tensor copies (mixed path, nx a multiple of 4).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
 
 #include "tpfa_impl.h"
 #include "tpfa_row.cuh"
@@ -89,6 +95,111 @@ static cudaError_t dispatch(AsmKernel kern, const GridGeom& g, const typename Ph
                         : launch_ymarch_t<Real, false, true, false>(g, q, f, o, JY, W, k0, k1, st);
     return jac ? launch_ymarch_t<Real, false, false, true>(g, q, f, o, JY, W, k0, k1, st)
                : launch_ymarch_t<Real, false, false, false>(g, q, f, o, JY, W, k0, k1, st);
+}
+
+// ------------------------------------------------------------------ TMA march
+
+// The TMA march runs 4 warps per block (4 x-segments: its halo boxes of
+// 136 cells stay within the copy engine's 256-element box limit), whatever
+// the tiling's warps per block.
+constexpr int kTmaWarps = 4;
+
+template <bool DIAG, bool CRK, bool JAC>
+static cudaError_t launch_tma_t(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const AsmOut<float>& o,
+                                const TmaMaps& maps, int JY, int k0, int k1, cudaStream_t st) {
+    constexpr int W = kTmaWarps;
+    constexpr int smem = ymarch_tma_smem_bytes<W, YMarch<float, DIAG, CRK, JAC, W>::TRING>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_assemble_ymarch_tma<DIAG, CRK, JAC, W>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 block(32, W, 1);
+    dim3 grid((g.nx + 32 * W - 1) / (32 * W), (g.ny + JY - 1) / JY, k1 - k0);
+    k_assemble_ymarch_tma<DIAG, CRK, JAC, W><<<grid, block, smem, st>>>(g, q, f, o, maps, JY, k0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_mixed_tma(const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
+                                      const AsmOut<float>& o, const TmaMaps& maps, int JY, int W, cudaStream_t st,
+                                      int k0, int k1) {
+    const bool jac = o.vals != nullptr;
+    if (k1 < 0 || k1 > g.nz) k1 = g.nz;
+    if (k0 < 0 || k0 % W != 0 || k0 >= k1) k0 = 0;  // the same plane ranges as the per-lane march
+    if (g.diag) {
+        if (crk) return jac ? launch_tma_t<true, true, true>(g, q, f, o, maps, JY, k0, k1, st)
+                            : launch_tma_t<true, true, false>(g, q, f, o, maps, JY, k0, k1, st);
+        return jac ? launch_tma_t<true, false, true>(g, q, f, o, maps, JY, k0, k1, st)
+                   : launch_tma_t<true, false, false>(g, q, f, o, maps, JY, k0, k1, st);
+    }
+    if (crk) return jac ? launch_tma_t<false, true, true>(g, q, f, o, maps, JY, k0, k1, st)
+                        : launch_tma_t<false, true, false>(g, q, f, o, maps, JY, k0, k1, st);
+    return jac ? launch_tma_t<false, false, true>(g, q, f, o, maps, JY, k0, k1, st)
+               : launch_tma_t<false, false, false>(g, q, f, o, maps, JY, k0, k1, st);
+}
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiled encoder() {
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// One (nx, ny, nz) field with a box of (bx, 1, bz) elements; out-of-range
+// elements of a box read as zero.
+bool encode_field(CUtensorMap* m, const GridGeom& g, const void* base, bool fp64, unsigned bx, unsigned bz) {
+    EncodeTiled fn = encoder();
+    if (!fn || !base || !aligned16(base)) return false;
+    const cuuint64_t es = fp64 ? 8 : 4;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nx * (cuuint64_t)g.ny * es};
+    const cuuint32_t box[3] = {bx, 1u, bz};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(m, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base),
+              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tma_grid_ok(const GridGeom& g) { return g.nx % 4 == 0 && encoder() != nullptr; }
+
+bool tma_encode_state(TmaMaps* m, const GridGeom& g, const float* p, const float* pn) {
+    using TS = TmaSlot<kTmaWarps>;
+    if (!tma_grid_ok(g)) return false;
+    return encode_field(&m->p, g, p, false, TS::HX, 3) && encode_field(&m->pn, g, pn, false, TS::SX, 1);
+}
+
+bool tma_encode_static(TmaMaps* m, const GridGeom& g, const AsmFields<float>& f, bool crk) {
+    using TS = TmaSlot<kTmaWarps>;
+    if (!tma_grid_ok(g)) return false;
+    bool ok = encode_field(&m->z, g, f.z, false, TS::HX, 3) && encode_field(&m->Tx, g, f.Tx, false, TS::HX, 1) &&
+              encode_field(&m->Ty, g, f.Ty, false, TS::SX, 1) && encode_field(&m->Tz, g, f.Tz, false, TS::SX, 2) &&
+              encode_field(&m->Tpp, g, f.Tpp, false, TS::HX, 1) && encode_field(&m->Tmp, g, f.Tmp, false, TS::HX, 1) &&
+              encode_field(&m->mn, g, f.mn, true, TS::SX, 1);
+    // phi0 is read only when c_r != 0; otherwise its map aliases z's
+    ok = ok && encode_field(&m->phi, g, crk ? (const void*)f.phi0 : (const void*)f.z, false, TS::SX, 1);
+    return ok;
 }
 
 cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk,

@@ -41,5 +41,6 @@ struct AsmOut {
 
 constexpr unsigned int STATUS_NONFINITE = 1u;
 constexpr unsigned int STATUS_DEVICE_CHECK = 2u;  // a checked device access was out of range
+constexpr unsigned int STATUS_TIMEOUT = 4u;       // a bounded device-side wait ran out
 
 }  // namespace tpfa

@@ -6,13 +6,14 @@
 #include "../../include/tpfa.h"
 #include "tpfa_grid.h"
 #include "tpfa_mesh.h"
+#include "tpfa_tma.cuh"
 
 namespace tpfa {
 
 struct PhysF;
 struct PhysD;
 
-enum class AsmKernel { Naive, YMarch };
+enum class AsmKernel { Naive, YMarch, YMarchTma };
 
 // JY: rows per warp march; W: warps (z-planes) per block, 4 or 8.  The tiled
 // kernel may be restricted to the planes [k0, k1) (k0 a multiple of W; rows
@@ -23,6 +24,17 @@ cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF
 cudaError_t launch_assemble_fp64(AsmKernel kern, const GridGeom& g, const PhysD& q, bool crk,
                                  const AsmFields<double>& f, const AsmOut<double>& o, int JY, int W,
                                  cudaStream_t st, int k0 = 0, int k1 = -1);
+// The mixed march with TMA row loads (same rows, same bits).  The maps come
+// from tma_encode_state (p, p^n: whenever the bound pointers change) and
+// tma_encode_static (the library-owned fields); both return false when the
+// grid (nx not a multiple of 4) or a pointer (not 16-byte aligned) rules TMA
+// out, or the driver offers no tensor-map encoder.
+cudaError_t launch_assemble_mixed_tma(const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
+                                      const AsmOut<float>& o, const TmaMaps& maps, int JY, int W, cudaStream_t st,
+                                      int k0 = 0, int k1 = -1);
+bool tma_grid_ok(const GridGeom& g);
+bool tma_encode_state(TmaMaps* m, const GridGeom& g, const float* p, const float* pn);
+bool tma_encode_static(TmaMaps* m, const GridGeom& g, const AsmFields<float>& f, bool crk);
 
 // Setup kernels (tpfa_setup.cu).
 struct SetupPhys {

@@ -44,6 +44,7 @@
 #include <type_traits>
 
 #include "tpfa_row.cuh"
+#include "tpfa_tma.cuh"
 
 namespace tpfa {
 
@@ -279,6 +280,134 @@ struct YMarch {
     __device__ __forceinline__ YRow<Real> row_cells(int sl) const {
         const Real* R = ring + sl * (NF * 32) + lane;
         return make_row(R[F_P * 32], R[F_Z * 32], R[F_HP * 32], R[F_HZ * 32]);
+    }
+
+    // ---- the same row inputs delivered by TMA (the mixed assembly march on
+    // grids whose x-rows are 16-byte multiples): the block's W warps own W
+    // consecutive x-segments of one plane and share a ring of TRING slots
+    // (TmaSlot<W>), each with a "full" mbarrier (one arrival plus the
+    // transaction bytes) and an "empty" one (one arrival per warp).  Thread
+    // (0, 0) of the block issues every copy; every lane waits on "full".
+    static constexpr int TRING = 3;  // slots: rows j-1 (until its refill), j, j+1, ...
+    using TS = TmaSlot<W>;
+    unsigned char* tring = nullptr;  // the block's first slot (128-byte aligned)
+    uint32_t tslot0 = 0, tfull0 = 0, tempty0 = 0;  // shared addresses: first slot, first full / empty barrier
+    const TmaMaps* tm = nullptr;
+    unsigned tphase = 0u;  // per slot: parity of its next "full" completion
+    unsigned ephase = 0u;  // per slot: parity of its next "empty" completion (issuing thread)
+    unsigned tpend = 0u;   // per slot: requested and not yet awaited
+    int xo = 0;            // this warp's segment within the block's boxes (cells)
+    int hx = 0;            // index in a halo box row of the value this lane takes as its x-halo
+    bool issuer = false;   // thread (0, 0) of the block
+
+    // Set up the shared ring (slots, TRING full then TRING empty barriers);
+    // every thread of the block calls it (it ends with a block barrier).
+    __device__ __forceinline__ void tma_init(unsigned char* slots, uint64_t* bars, const TmaMaps* maps, int w) {
+        tring = slots;
+        tslot0 = smem_u32(slots);
+        tfull0 = smem_u32(bars);
+        tempty0 = tfull0 + 8u * TRING;
+        tm = maps;
+        xo = 32 * w;
+        hx = xo + (lane == 0 ? 3 : (lane == 31 ? 36 : 4 + lane));
+        issuer = w == 0 && lane == 0;
+        if (issuer) {
+            for (int s = 0; s < TRING; ++s) {
+                mbar_init(tfull0 + 8u * s, 1u);
+                mbar_init(tempty0 + 8u * s, (unsigned)W);
+            }
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
+    // Thread (0, 0): request every box of row r (block x-range from X0, plane
+    // k) into slot sl; with `refill`, first wait until every warp has
+    // released the slot.  False if that wait ran out (nothing is issued).
+    __device__ __forceinline__ bool tma_issue(int r, int sl, int X0, bool refill) {
+        if (refill) {
+            if (!mbar_wait_bounded(tempty0 + 8u * sl, (ephase >> sl) & 1u)) return false;
+            ephase ^= 1u << sl;
+        }
+        const uint32_t d = tslot0 + (uint32_t)(sl * TS::BYTES), b = tfull0 + 8u * sl;
+        const int xh = X0 - 4;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(b, TS::tx_bytes(DIAG, CRK));
+        tma_load_3d(d + TS::P, &tm->p, xh, r, k - 1, b);
+        tma_load_3d(d + TS::Z, &tm->z, xh, r, k - 1, b);
+        tma_load_3d(d + TS::TX, &tm->Tx, xh, r, k, b);
+        tma_load_3d(d + TS::TY, &tm->Ty, X0, r, k, b);
+        tma_load_3d(d + TS::TZ, &tm->Tz, X0, r, k - 1, b);
+        if (DIAG) {
+            tma_load_3d(d + TS::TPP, &tm->Tpp, xh, r, k, b);
+            tma_load_3d(d + TS::TMP, &tm->Tmp, xh, r, k, b);
+        }
+        tma_load_3d(d + TS::PN, &tm->pn, X0, r, k, b);
+        if (CRK) tma_load_3d(d + TS::PHI, &tm->phi, X0, r, k, b);
+        tma_load_3d(d + TS::MN, &tm->mn, X0, r, k, b);
+        return true;
+    }
+    // Every warp: the row requested into slot sl is now expected.
+    __device__ __forceinline__ void tma_requested(int sl) { tpend |= 1u << sl; }
+    // This warp is done with slot sl.
+    __device__ __forceinline__ void tma_release(int sl) const {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8u * sl);
+    }
+    // Wait for slot sl's row; false (for the whole warp) if the wait ran out.
+    __device__ __forceinline__ bool tma_wait(int sl) {
+        bool ok = mbar_wait_bounded(tfull0 + 8u * sl, (tphase >> sl) & 1u);
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) {
+            tphase ^= 1u << sl;
+            tpend &= ~(1u << sl);
+        }
+        return ok;
+    }
+    // Wait (bounded) for every slot still expected; false if one ran out.
+    __device__ __forceinline__ bool tma_drain() {
+        bool ok = true;
+        for (int s = 0; s < TRING; ++s)
+            if ((tpend >> s) & 1u) ok = tma_wait(s) && ok;
+        return ok;
+    }
+    __device__ __forceinline__ const float* tma_slot(int sl) const {
+        return reinterpret_cast<const float*>(tring + sl * TS::BYTES);
+    }
+    __device__ __forceinline__ YRow<Real> tma_row_cells(int sl) const {
+        const float* S = tma_slot(sl);
+        constexpr int P1 = TS::P / 4 + TS::HX, Z1 = TS::Z / 4 + TS::HX;  // plane k
+        return make_row(S[P1 + xo + 4 + lane], S[Z1 + xo + 4 + lane], S[P1 + hx], S[Z1 + hx]);
+    }
+    // The diagonal-link T of lanes 0 and 31 into row r - 1 (Tpp(i0 - 1, r - 1)
+    // and Tmp(i0 + 32, r - 1)), read from the slot of row r - 1 before it is
+    // refilled; 0 in the other lanes.
+    __device__ __forceinline__ Real tma_h2(int sl) const {
+        if (!DIAG) return Real(0);
+        const float* S = tma_slot(sl);
+        const float t = lane == 31 ? S[TS::TMP / 4 + xo + 36] : S[TS::TPP / 4 + xo + 3];
+        return (lane == 0 || lane == 31) ? t : 0.f;
+    }
+    __device__ __forceinline__ YIn<Real> tma_read_in(int sl, Real hT2) const {
+        const float* S = tma_slot(sl);
+        constexpr int P0 = TS::P / 4, Z0 = TS::Z / 4, B = TS::HX;
+        const int o = xo + lane, oh = o + 4;  // the lane's cell in a plain box row and in a halo box row
+        YIn<Real> D;
+        D.Tx = S[TS::TX / 4 + oh];
+        D.Ty = S[TS::TY / 4 + o];
+        D.Tz = S[TS::TZ / 4 + TS::SX + o];
+        D.Tpp = DIAG ? S[TS::TPP / 4 + oh] : Real(0);
+        D.Tmp = DIAG ? S[TS::TMP / 4 + oh] : Real(0);
+        D.pn = S[TS::PN / 4 + o];
+        D.phi0 = CRK ? S[TS::PHI / 4 + o] : Real(0);
+        D.mn = reinterpret_cast<const double*>(tring + sl * TS::BYTES + TS::MN)[o];
+        D.p_zm = S[P0 + oh];
+        D.z_zm = S[Z0 + oh];
+        D.Tz_m = S[TS::TZ / 4 + o];
+        D.p_zp = S[P0 + 2 * B + oh];
+        D.z_zp = S[Z0 + 2 * B + oh];
+        D.hT1 = lane == 0 ? S[TS::TX / 4 + xo + 3] : Real(0);  // Tx(i0 - 1, r)
+        D.hT2 = hT2;
+        return D;
     }
 
     // w of the row in ring slot sl, narrowed to FP32 on the integer pipe
@@ -717,6 +846,108 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
         for (int b = 0; b < 64; ++b)
             if ((tie_rows >> b) & 1ull) naive_row<Real, CRK, JAC>(g, q, f, o, M.act, M.i, j0 + b, k);
     }
+}
+
+// Dynamic shared memory of one block of the TMA march: the shared ring of
+// TRING slots, per warp two CSR staging buffers, 2 TRING mbarriers, and
+// slack to align the ring to 128 bytes.
+template <int W, int TRING>
+constexpr int ymarch_tma_smem_bytes() {
+    return 128 + TRING * TmaSlot<W>::BYTES + W * 2 * (32 * NSLOT + 4) * 4 + 2 * TRING * 8;
+}
+
+// The march with its row inputs delivered by TMA (mixed path): block (bx,
+// by, k) runs the W x-segments bx W .. bx W + W - 1 of plane k over the
+// y-run by, one warp per segment, all warps stepping through a shared ring.
+// Every row is computed by the same code as in ymarch_tile, so the results
+// are bit-identical.  Warps whose segment lies past the grid's x-extent only
+// keep the ring's protocol.  A barrier wait that runs out sets
+// STATUS_TIMEOUT and ends the march (after a bounded wait for the copies
+// still in flight).
+template <bool DIAG, bool CRK, bool JAC, int W>
+__device__ __forceinline__ void ymarch_tile_tma(const GridGeom& g, const PhysF& q, const AsmFields<float>& f,
+                                                const AsmOut<float>& o, const TmaMaps* maps, int JY, int bx,
+                                                int by, int k, unsigned char* smem) {
+    using M_t = YMarch<float, DIAG, CRK, JAC, W>;
+    using TS = TmaSlot<W>;
+    constexpr int BUF = 32 * NSLOT + 4, TR = M_t::TRING;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+    float* stage = reinterpret_cast<float*>(base + TR * TS::BYTES) + w * 2 * BUF;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + TR * TS::BYTES + W * 2 * BUF * 4);
+    const int X0 = bx * 32 * W;
+    M_t M(g, q, f, o, lane, X0 + 32 * w, k);
+    M.tma_init(base, bars, maps, w);
+    const bool live = M.i0 < g.nx;  // warp-uniform
+    const int j0 = by * JY;
+    const int j1 = min(j0 + JY, g.ny);
+    const bool zint = M.zm && M.zp;
+
+    bool ok = true;
+    if (M.issuer) {
+        for (int s = 0; s < TR; ++s) M.tma_issue(j0 - 1 + s, s, X0, false);
+    }
+    for (int s = 0; s < TR; ++s) M.tma_requested(s);
+    ok = M.tma_wait(0);
+    ok = ok && M.tma_wait(1);
+    unsigned long long tie_rows = 0ull;
+    if (ok) {
+        YRow<float> P = M.tma_row_cells(0);
+        YRow<float> C = M.tma_row_cells(1);
+        YUp<float> U;
+        {
+            const YIn<float> Dp = M.tma_read_in(0, 0.f);
+            U = M.up_links(P, C, Dp.Ty, Dp.Tpp, Dp.Tmp);
+        }
+        int sp = 0;  // slot of row j-1; rows j, j+1, ... follow in the next slots (mod TR)
+        int rowbase = M.row_base(j0);
+        for (int j = j0; j < j1; ++j) {
+            const int s0 = sp + 1 == TR ? 0 : sp + 1;
+            const int s1 = s0 + 1 == TR ? 0 : s0 + 1;
+            const float hT2 = M.tma_h2(sp);  // slot sp holds row j-1 until the refill below
+            M.tma_release(sp);
+            if (M.issuer && !M.tma_issue(j + TR - 1, sp, X0, true)) atomicOr(o.status, STATUS_TIMEOUT);
+            M.tma_requested(sp);
+            if (!M.tma_wait(s1)) {
+                ok = false;
+                break;
+            }
+            const YRow<float> N = M.tma_row_cells(s1);
+            const YIn<float> D = M.tma_read_in(s0, hT2);
+            sp = s0;
+            if (live) {
+                float* buf = stage + ((j - j0) & 1) * BUF;
+                M.buffer_ready();
+                if (__any_sync(0xffffffffu, U.tie)) tie_rows |= 1ull << (j - j0);
+                const bool injk = zint && j > 0 && j + 1 < M.ny;
+                if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, buf, rowbase);
+                else if (injk) U = M.template row<1>(j, P, C, N, D, U, buf, rowbase);
+                else U = M.template row<0>(j, P, C, N, D, U, buf, rowbase);
+                rowbase += M.row_base_step(j);
+            }
+            P = C;
+            C = N;
+        }
+    }
+    ok = M.tma_drain() && ok;
+    M.drain();
+    if (!ok) {
+        if (lane == 0) atomicOr(o.status, STATUS_TIMEOUT);
+        return;
+    }
+    if (tie_rows) {  // warp-uniform; every bulk store of the warp has completed
+        __syncwarp();
+        for (int b = 0; b < 64; ++b)
+            if ((tie_rows >> b) & 1ull) naive_row<float, CRK, JAC>(g, q, f, o, M.act, M.i, j0 + b, k);
+    }
+}
+
+template <bool DIAG, bool CRK, bool JAC, int W>
+__global__ void __launch_bounds__(32 * W, 16 / W)
+    k_assemble_ymarch_tma(GridGeom g, PhysF q, AsmFields<float> f, AsmOut<float> o, const __grid_constant__ TmaMaps tm,
+                          int JY, int k0) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ymarch_tile_tma<DIAG, CRK, JAC, W>(g, q, f, o, &tm, JY, blockIdx.x, blockIdx.y, k0 + (int)blockIdx.z, smem);
 }
 
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>

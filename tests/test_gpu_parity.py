@@ -27,8 +27,10 @@ def _grid(prob, precision):
     return Grid(prob.nx, prob.ny, prob.nz, prob.phys, precision, prob.perm, prob.poro, prob.depth)
 
 
-def run_gpu(prob, precision, kernel="auto"):
+def run_gpu(prob, precision, kernel="auto", tiling=None):
     with _grid(prob, precision) as g:
+        if tiling is not None:
+            g.set_tiling(*tiling)
         g.set_state(prob.p, prob.pn)
         R, vals, diag = g.assemble_jacobian(kernel=kernel)
         g.sync_status()
@@ -96,6 +98,81 @@ def test_kernel_variants_bit_identical(shape, conn, precision, c_r):
     assert np.array_equal(a["vals"], b["vals"])
     if precision == "mixed":
         assert np.array_equal(a["diag"].view(np.uint64), b["diag"].view(np.uint64))
+
+
+def _same_bits(a, b, precision):
+    assert np.array_equal(a["R"].view(np.uint64), b["R"].view(np.uint64))
+    assert np.array_equal(a["vals"].view(np.uint32 if precision == "mixed" else np.uint64),
+                          b["vals"].view(np.uint32 if precision == "mixed" else np.uint64))
+    if precision == "mixed":
+        assert np.array_equal(a["diag"].view(np.uint64), b["diag"].view(np.uint64))
+
+
+# nx a multiple of 4 (the TMA march's condition): one partial segment, a
+# segment plus a ragged 4-cell tail, several segments with ragged y-runs, a
+# single row, and more planes than a block holds.
+TMA_SHAPES = [(4, 3, 2), (36, 5, 3), (72, 41, 11), (128, 66, 9), (64, 1, 5)]
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("conn", [6, 10])
+@pytest.mark.parametrize("c_r", [0.0, 1e-9])
+def test_tma_march_bit_identical(shape, conn, c_r):
+    """The march with its row inputs delivered as TMA boxes (elements outside
+    the grid zero-filled by the copy engine; x-segments past the grid's
+    extent only keep the ring's protocol) gives the naive kernel's bits
+    under every tiling, and so does the library's automatic choice."""
+    prob = problem(shape, conn, "mixed", c_r=c_r, seed=5)
+    a = run_gpu(prob, "mixed", "naive")
+    for tiling in [(32, 4), (1, 8), (7, 4), (64, 8)]:
+        _same_bits(a, run_gpu(prob, "mixed", "tiled_tma", tiling=tiling), "mixed")
+    _same_bits(a, run_gpu(prob, "mixed", "auto"), "mixed")
+
+
+def test_tma_march_follows_the_bound_pressure():
+    """The tensor map of p is re-encoded when the bound pointer changes
+    (set_pressure, set_state): each call assembles the pressure bound at
+    that moment."""
+    base = problem((72, 40, 9), 10, "mixed", seed=8)
+    ps = [base.p] + synth.pressure_sequence(base, 2, seed=4)
+    with _grid(base, "mixed") as g:
+        g.set_state(ps[0], base.pn)
+        for p in ps + [ps[0]]:
+            g.set_pressure(p)
+            R_t, v_t, d_t = (x.clone() for x in g.assemble_jacobian(kernel="tiled_tma"))
+            R_n, v_n, d_n = g.assemble_jacobian(kernel="naive")
+            torch.cuda.synchronize()
+            assert torch.equal(R_t, R_n) and torch.equal(v_t, v_n) and torch.equal(d_t, d_n)
+        g.sync_status()
+
+
+def test_tma_march_conditions():
+    """The TMA march refuses what it cannot load (nx not a multiple of 4, an
+    FP64 grid, a pressure pointer off a 16-byte boundary); the automatic
+    choice (the per-lane march) still assembles such a state, with the naive
+    kernel's bits."""
+    from paper_2304_11274_gb300.api import TPFAError
+    for shape, precision in [((70, 9, 5), "mixed"), ((72, 9, 5), "fp64")]:
+        prob = problem(shape, 10, precision)
+        with _grid(prob, precision) as g:
+            g.set_state(prob.p, prob.pn)
+            with pytest.raises(TPFAError) as ei:
+                g.assemble_jacobian(kernel="tiled_tma")
+            assert ei.value.name == "TPFA_ERR_INVALID_ARG"
+    prob = problem((72, 9, 5), 10, "mixed")
+    buf = torch.zeros(prob.n + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.as_tensor(prob.p, dtype=torch.float32, device="cuda")
+    p_off = buf[1:]  # 4 bytes past a 16-byte boundary
+    with _grid(prob, "mixed") as g:
+        g.set_state(p_off, prob.pn)
+        with pytest.raises(TPFAError) as ei:
+            g.assemble_jacobian(kernel="tiled_tma")
+        assert ei.value.name == "TPFA_ERR_INVALID_ARG"
+        R_a, v_a, d_a = (x.clone() for x in g.assemble_jacobian(kernel="auto"))
+        R_n, v_n, d_n = g.assemble_jacobian(kernel="naive")
+        torch.cuda.synchronize()
+        assert torch.equal(R_a, R_n) and torch.equal(v_a, v_n) and torch.equal(d_a, d_n)
+        g.sync_status()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -326,8 +403,5 @@ def test_reused_link_ties_are_fixed_up(precision, conn):
         vertical = (rows >= prob.nx) & (ref["col_idx"] < prob.nx)  # row-1 cells' links into row 0
         assert np.any(ref["dphi"][vertical] == 0.0)
     a = run_gpu(prob, precision, "naive")
-    b = run_gpu(prob, precision, "tiled")
-    assert np.array_equal(a["R"].view(np.uint64), b["R"].view(np.uint64))
-    assert np.array_equal(a["vals"], b["vals"])
-    if precision == "mixed":
-        assert np.array_equal(a["diag"].view(np.uint64), b["diag"].view(np.uint64))
+    for kernel in ["tiled", "tiled_tma"] if precision == "mixed" else ["tiled"]:
+        _same_bits(a, run_gpu(prob, precision, kernel), precision)
