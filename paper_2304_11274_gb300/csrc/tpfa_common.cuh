@@ -136,6 +136,43 @@ struct PhysD {
     double rho_ref, p_ref, c_f, inv_mu, g, half_g, V_dt, c_r;
 };
 
+// exp(x) and expm1(x) in FP64 for the small arguments the state equation
+// meets (|x| < 2^-5: c_f (p - p_ref) with c_f ~ 1e-9 / Pa and pressures
+// within tens of MPa of p_ref) by their Taylor series, cut after x^8 (exp)
+// and x^9 (expm1): the remainder is below 2^-60 of the value, so the result
+// is the function's within the few roundings of the Horner steps.  Larger
+// arguments (and NaN or infinity) take exp() / expm1().  The FP64 path is
+// bound by the FP64 pipe, and these series need fewer FP64 instructions per
+// exponential call.  The range test reads the high word (integer pipe).
+__device__ __forceinline__ bool small_arg(double x) {
+    return ((uint32_t)__double2hiint(x) & 0x7fffffffu) < 0x3fa00000u;  // |x| < 2^-5
+}
+__device__ __forceinline__ double exp_fp64(double x) {
+    if (!small_arg(x)) return exp(x);
+    double r = 1.0 / 40320.0;  // 1/8!
+    r = __fma_rn(r, x, 1.0 / 5040.0);
+    r = __fma_rn(r, x, 1.0 / 720.0);
+    r = __fma_rn(r, x, 1.0 / 120.0);
+    r = __fma_rn(r, x, 1.0 / 24.0);
+    r = __fma_rn(r, x, 1.0 / 6.0);
+    r = __fma_rn(r, x, 0.5);
+    r = __fma_rn(r, x, 1.0);
+    return __fma_rn(r, x, 1.0);
+}
+__device__ __forceinline__ double expm1_fp64(double x) {
+    if (!small_arg(x)) return expm1(x);
+    double r = 1.0 / 362880.0;  // 1/9!: expm1(x) = x (1 + x/2! + x^2/3! + ... + x^8/9!)
+    r = __fma_rn(r, x, 1.0 / 40320.0);
+    r = __fma_rn(r, x, 1.0 / 5040.0);
+    r = __fma_rn(r, x, 1.0 / 720.0);
+    r = __fma_rn(r, x, 1.0 / 120.0);
+    r = __fma_rn(r, x, 1.0 / 24.0);
+    r = __fma_rn(r, x, 1.0 / 6.0);
+    r = __fma_rn(r, x, 0.5);
+    r = __fma_rn(r, x, 1.0);
+    return __dmul_rn(r, x);
+}
+
 // Eq. density: rho = rho_ref exp(c_f (p - p_ref)), and its derivative.
 __device__ __forceinline__ CellVal<float> make_cell(const PhysF& q, float p, float z) {
     CellVal<float> c;
@@ -149,7 +186,7 @@ __device__ __forceinline__ CellVal<double> make_cell(const PhysD& q, double p, d
     CellVal<double> c;
     c.p = p;
     c.z = z;
-    c.rho = __dmul_rn(q.rho_ref, exp(__dmul_rn(q.c_f, __dsub_rn(p, q.p_ref))));
+    c.rho = __dmul_rn(q.rho_ref, exp_fp64(__dmul_rn(q.c_f, __dsub_rn(p, q.p_ref))));
     c.drho = __dmul_rn(q.c_f, c.rho);
     return c;
 }
@@ -166,20 +203,22 @@ struct LinkOut {
 // Two-point flux of Eq. flux-calc seen from row a (z = depth, positive down):
 //   dPhi = (p_a - p_b) - rho_avg g (z_a - z_b)
 //   upstream = a if dPhi > 0 else b,  F = T (rho_up / mu) dPhi
-// and its two pressure derivatives.  Negating every input that changes sign
-// between the two ends of a link negates every output, so F_ba = -F_ab
-// exactly (except the derivatives at an exact tie dPhi == 0, where each end
-// takes the other cell as upstream).
+// and its two pressure derivatives.  rho_avg g dz is formed as
+// (rho_a + rho_b)(g/2 dz): halving is exact, so the fused product equals
+// the one of rho_avg and g dz bit for bit, with two multiplications fewer;
+// T/mu is formed once and scales both rho_up and dPhi.  Negating every input
+// that changes sign between the two ends of a link negates every output, so
+// F_ba = -F_ab exactly (except the derivatives at an exact tie dPhi == 0,
+// where each end takes the other cell as upstream).
 __device__ __forceinline__ LinkOut<float> link(const PhysF& q, float T, const CellVal<float>& a,
                                                const CellVal<float>& b) {
     const float dp = __fsub_rn(a.p, b.p);
-    const float gdz = __fmul_rn(q.g, __fsub_rn(a.z, b.z));
     const float hgdz = __fmul_rn(q.half_g, __fsub_rn(a.z, b.z));
-    const float rbar = __fmul_rn(0.5f, __fadd_rn(a.rho, b.rho));
-    const float dphi = __fmaf_rn(-rbar, gdz, dp);
+    const float dphi = __fmaf_rn(-__fadd_rn(a.rho, b.rho), hgdz, dp);
     const bool up_a = dphi > 0.f;
-    const float Tl = __fmul_rn(T, __fmul_rn(up_a ? a.rho : b.rho, q.inv_mu));
-    const float w = __fmul_rn(__fmul_rn(T, q.inv_mu), dphi);
+    const float Tm = __fmul_rn(T, q.inv_mu);
+    const float Tl = __fmul_rn(Tm, up_a ? a.rho : b.rho);
+    const float w = __fmul_rn(Tm, dphi);
     LinkOut<float> r;
     r.F = __fmul_rn(Tl, dphi);
     const float dda = __fmaf_rn(-a.drho, hgdz, 1.f);
@@ -192,19 +231,18 @@ __device__ __forceinline__ LinkOut<float> link(const PhysF& q, float T, const Ce
 __device__ __forceinline__ LinkOut<double> link(const PhysD& q, double T, const CellVal<double>& a,
                                                 const CellVal<double>& b) {
     const double dp = __dsub_rn(a.p, b.p);
-    const double gdz = __dmul_rn(q.g, __dsub_rn(a.z, b.z));
     const double hgdz = __dmul_rn(q.half_g, __dsub_rn(a.z, b.z));
-    const double rbar = __dmul_rn(0.5, __dadd_rn(a.rho, b.rho));
-    const double dphi = __fma_rn(-rbar, gdz, dp);
+    const double dphi = __fma_rn(-__dadd_rn(a.rho, b.rho), hgdz, dp);
     const bool up_a = dphi > 0.0;
-    const double Tl = __dmul_rn(T, __dmul_rn(up_a ? a.rho : b.rho, q.inv_mu));
-    const double w = __dmul_rn(__dmul_rn(T, q.inv_mu), dphi);
+    const double Tm = __dmul_rn(T, q.inv_mu);
+    const double Tl = __dmul_rn(Tm, up_a ? a.rho : b.rho);
+    const double w = __dmul_rn(Tm, dphi);
     LinkOut<double> r;
     r.F = __dmul_rn(Tl, dphi);
     const double dda = __fma_rn(-a.drho, hgdz, 1.0);
     const double ddb = __fma_rn(-b.drho, hgdz, -1.0);
-    r.Da = __fma_rn(Tl, dda, up_a ? __dmul_rn(a.drho, w) : 0.0);
-    r.Db = __fma_rn(Tl, ddb, up_a ? 0.0 : __dmul_rn(b.drho, w));
+    r.Da = __fma_rn(Tl, dda, __dmul_rn(up_a ? a.drho : 0.0, w));
+    r.Db = __fma_rn(Tl, ddb, __dmul_rn(up_a ? 0.0 : b.drho, w));
     return r;
 }
 
@@ -225,14 +263,12 @@ struct Link2 {
 __device__ __forceinline__ Link2 link2(const PhysF& q, float2 T, const CellVal<float>& a, const CellVal<float>& b0,
                                        const CellVal<float>& b1) {
     const float2 dp = __fadd2_rn(f2(a.p), neg2(f2(b0.p, b1.p)));
-    const float2 dz = __fadd2_rn(f2(a.z), neg2(f2(b0.z, b1.z)));
-    const float2 gdz = __fmul2_rn(f2(q.g), dz);
-    const float2 hgdz = __fmul2_rn(f2(q.half_g), dz);
-    const float2 rbar = __fmul2_rn(f2(0.5f), __fadd2_rn(f2(a.rho), f2(b0.rho, b1.rho)));
-    const float2 dphi = __ffma2_rn(neg2(rbar), gdz, dp);
+    const float2 hgdz = __fmul2_rn(f2(q.half_g), __fadd2_rn(f2(a.z), neg2(f2(b0.z, b1.z))));
+    const float2 dphi = __ffma2_rn(neg2(__fadd2_rn(f2(a.rho), f2(b0.rho, b1.rho))), hgdz, dp);
     const bool u0 = dphi.x > 0.f, u1 = dphi.y > 0.f;
-    const float2 Tl = __fmul2_rn(T, __fmul2_rn(f2(u0 ? a.rho : b0.rho, u1 ? a.rho : b1.rho), f2(q.inv_mu)));
-    const float2 w = __fmul2_rn(__fmul2_rn(T, f2(q.inv_mu)), dphi);
+    const float2 Tm = __fmul2_rn(T, f2(q.inv_mu));
+    const float2 Tl = __fmul2_rn(Tm, f2(u0 ? a.rho : b0.rho, u1 ? a.rho : b1.rho));
+    const float2 w = __fmul2_rn(Tm, dphi);
     Link2 r;
     r.F = __fmul2_rn(Tl, dphi);
     const float2 dda = __ffma2_rn(neg2(f2(a.drho)), hgdz, f2(1.f));
@@ -295,7 +331,7 @@ template <bool CR>
 __device__ __forceinline__ AccD accumulation(const PhysD& q, double p, double pn, double mn, double rho,
                                              double phi0) {
     const double dpn = __dsub_rn(p, pn);
-    const double e = expm1(__dmul_rn(q.c_f, dpn));
+    const double e = expm1_fp64(__dmul_rn(q.c_f, dpn));
     AccD r;
     r.A = __dmul_rn(mn, e);
     if (CR) {
