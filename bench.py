@@ -58,20 +58,25 @@ def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
 FP64_PEAK_TOPS = 0.625  # nominal GB300 FP64: 1.25 TFLOP/s, i.e. 0.625 T FMA instructions/s
 
 
-def fp64_ops_per_cell():
+def fp64_ops_per_cell(kernel_hash: str):
     """FP64 instructions per cell of the FP64 assembly kernel, from the
-    committed ncu count (None if absent)."""
+    committed ncu count, if it was taken on the current kernel source (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "assemble_fp64_256x256x128_ops.md")
     if not os.path.exists(path):
         return None
+    vals = {}
     with open(path) as fh:
         for line in fh:
-            if line.strip().startswith("- `fp64_ops_per_cell`"):
-                try:
-                    return float(line.split("`")[3])
-                except (IndexError, ValueError):
-                    return None
-    return None
+            if ":" in line and line.strip().startswith("- `"):
+                key, _, v = line.strip()[3:].partition("`:")
+                vals[key.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_hash:
+        return None
+    try:
+        return float(vals["fp64_ops_per_cell"])
+    except (KeyError, ValueError):
+        return None
 
 
 def measured_peaks():
@@ -198,7 +203,7 @@ def run_ours(args):
 
     def step(s):
         g.set_pressure(p_dev[s % len(p_dev)])
-        g.assemble_jacobian(R, vals, diag)
+        g.assemble_jacobian(R, vals, diag, kernel=args.kernel)
 
     for s in range(args.warmup):
         step(s)
@@ -244,7 +249,9 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = nbytes / avg_launch_s / 1e9
     khash = kernel_source_hash()
-    traffic = profiled_traffic(khash)
+    tma = args.kernel == "tiled_tma"
+    kname = "k_assemble_ymarch_tma<DIAG,!CR,JAC,W=4>" if tma else "k_assemble_ymarch<float,DIAG,!CR,JAC>"
+    traffic = profiled_traffic(khash, "assemble_tma_mixed_512x512x256.md" if tma else "assemble_mixed_512x512x256.md")
 
     # end to end: host buffers through the C ABI (H2D of p, D2H of R, values, diag64)
     e2e = None
@@ -296,7 +303,7 @@ def run_ours(args):
         g64.sync_status()
         f_ms = a.elapsed_time(b) / nf
         b64 = algorithmic_bytes(prob.n, g64.nnz, "fp64")
-        ops = fp64_ops_per_cell()
+        ops = fp64_ops_per_cell(kernel_source_hash())
         rate = prob.n / (f_ms * 1e-3)
         fp64 = {"value": rate, "unit": "cells/s", "ms_per_step": f_ms,
                 "hbm_GBps": b64 / (f_ms * 1e-3) / 1e9, "hbm_frac": b64 / (f_ms * 1e-3) / 1e9 / peak,
@@ -331,10 +338,11 @@ def run_ours(args):
                    "nnz": g.nnz, "precision": "mixed: FP32 flux + Kahan residual, FP64 accumulation/diagonal/R",
                    "l2": "inputs+outputs 6.7 GB per step > 129 MB L2; no flush",
                    "pressure_vectors": len(pres), "parallelism": f"replicas x{world}",
-                   "tiling": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]}},
+                   "tiling": {"rows_per_march": tiling[0], "warps_per_block": 4 if tma else tiling[1]},
+                   "kernel_variant": args.kernel},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
-                     "kernel": "k_assemble_ymarch<float,DIAG,!CR,JAC>", "kernel_source_sha256_16": khash},
+                     "kernel": kname, "kernel_source_sha256_16": khash},
         "launch_ms": launch_stats,
         "clocks": clk,
         "e2e": e2e,
@@ -645,6 +653,8 @@ def main():
     ap.add_argument("--skip-jvp", action="store_true", help="skip the matrix-free J w line")
     ap.add_argument("--skip-newton", action="store_true", help="skip the Newton-step line")
     ap.add_argument("--skip-mesh", action="store_true", help="skip the general-mesh line")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "tiled_tma"],
+                    help="assembly kernel variant of the timed step (auto = the library's choice)")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
                     help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")
     args = ap.parse_args()
