@@ -179,11 +179,16 @@ __global__ void __launch_bounds__(256) k_dinv(GridGeom g, const Real* __restrict
 // the elimination multiplier l_k = sub_k / b'_{k-1}, the super-diagonal
 // u_k and the inverse pivot 1 / b'_k.  An application is one thread per
 // (i, j) column, a forward sweep y_k = in_k - l_k y_{k-1} and a backward
-// sweep z_k = (y_k - u_k z_{k+1}) / b'_k, each loading the next chunk of
-// steps while it computes the current one.
+// sweep z_k = (y_k - u_k z_{k+1}) / b'_k.  The columns are few (nx ny
+// threads) and each sweep is a chain of dependent steps, so the bandwidth
+// comes from loads in flight: every thread keeps its next kLineDepth steps'
+// operands on the way into a shared-memory ring (8-byte cp.async per value,
+// one commit group per step), one warp per block so that the 512 warps of a
+// 128 x 128 grid spread evenly over the multiprocessors.
 
-constexpr int kLineThreads = 64;
-constexpr int kChunk = 8;
+constexpr int kLineThreads = 64;  // the factorisation
+constexpr int kApplyThreads = 32;  // the application: one warp per block
+constexpr int kLineDepth = 16;     // steps in flight per column
 
 template <typename Real, bool MIXED>
 __global__ void __launch_bounds__(kLineThreads) k_line_factor(GridGeom g, const Real* __restrict__ vals,
@@ -215,81 +220,79 @@ __global__ void __launch_bounds__(kLineThreads) k_line_factor(GridGeom g, const 
     }
 }
 
-struct LineChunk {
-    double a[kChunk], b[kChunk], d[kChunk];
-};
+__device__ __forceinline__ void cp8_async(double* dst, const double* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-// out = M^-1 in; on the mixed path also out split into FP32 pairs.
-__global__ void __launch_bounds__(kLineThreads) k_line_apply(GridGeom g, const double* __restrict__ inv_b,
-                                                             const double* __restrict__ lmul,
-                                                             const double* __restrict__ up,
-                                                             const double* __restrict__ in, double* __restrict__ out,
-                                                             float* __restrict__ hi, float* __restrict__ lo,
-                                                             const KrylovScalars* S) {
+// out = M^-1 in; on the mixed path also out split into FP32 pairs.  Each
+// lane copies and reads back only its own ring entries.  A step's slot is
+// refilled only after the step's result has been computed from it (in-order
+// issue puts the reads first).
+__global__ void __launch_bounds__(kApplyThreads) k_line_apply(GridGeom g, const double* __restrict__ inv_b,
+                                                              const double* __restrict__ lmul,
+                                                              const double* __restrict__ up,
+                                                              const double* __restrict__ in, double* __restrict__ out,
+                                                              float* __restrict__ hi, float* __restrict__ lo,
+                                                              const KrylovScalars* S) {
+    __shared__ __align__(16) double ring[kLineDepth][3][kApplyThreads];
     if (S->done) return;
     const long long nxy = (long long)g.nx * g.ny;
-    const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long col = blockIdx.x * (long long)kApplyThreads + threadIdx.x;
     if (col >= nxy) return;
-    const int nz = g.nz;
-    const int nch = (nz + kChunk - 1) / kChunk;
+    const int nz = g.nz, l = threadIdx.x;
     // forward: y_k = in_k - l_k y_{k-1}
-    auto load_f = [&](int q, LineChunk& L) {
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-            const int k = q * kChunk + u;
-            const bool ok = k < nz;
-            const long long c = col + nxy * (ok ? k : 0);
-            L.a[u] = ok ? in[c] : 0.0;
-            L.b[u] = ok ? lmul[c] : 0.0;
+    auto issue_f = [&](int k) {
+        if (k < nz) {
+            const long long c = col + nxy * k;
+            cp8_async(&ring[k % kLineDepth][0][l], in + c);
+            cp8_async(&ring[k % kLineDepth][1][l], lmul + c);
         }
+        cp_commit();
     };
-    LineChunk A, B;
-    load_f(0, A);
+    for (int k = 0; k < kLineDepth; ++k) issue_f(k);
     double y = 0.0;
-    for (int q = 0; q < nch; ++q) {
-        if (q + 1 < nch) load_f(q + 1, B);
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-            const int k = q * kChunk + u;
-            if (k < nz) {
-                y = fma(-A.b[u], y, A.a[u]);
-                out[col + nxy * k] = y;
-            }
-        }
-        A = B;
+    for (int k = 0; k < nz; ++k) {
+        cp_wait<kLineDepth - 1>();
+        const int sl = k % kLineDepth;
+        y = fma(-ring[sl][1][l], y, ring[sl][0][l]);
+        out[col + nxy * k] = y;
+        issue_f(k + kLineDepth);
     }
+    cp_wait<0>();
+    __threadfence_block();  // y stored above is read back below by this thread
     // back: z_k = (y_k - u_k z_{k+1}) / b'_k, steps k = nz-1 down to 0
-    auto load_b = [&](int q, LineChunk& L) {
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-            const int k = nz - 1 - (q * kChunk + u);
-            const bool ok = k >= 0;
-            const long long c = col + nxy * (ok ? k : 0);
-            L.a[u] = ok ? out[c] : 0.0;
-            L.b[u] = ok ? up[c] : 0.0;
-            L.d[u] = ok ? inv_b[c] : 0.0;
+    auto issue_b = [&](int q) {
+        const int k = nz - 1 - q;
+        if (k >= 0) {
+            const long long c = col + nxy * k;
+            cp8_async(&ring[q % kLineDepth][0][l], out + c);
+            cp8_async(&ring[q % kLineDepth][1][l], up + c);
+            cp8_async(&ring[q % kLineDepth][2][l], inv_b + c);
         }
+        cp_commit();
     };
-    load_b(0, A);
+    for (int q = 0; q < kLineDepth; ++q) issue_b(q);
     double z = 0.0;
-    for (int q = 0; q < nch; ++q) {
-        if (q + 1 < nch) load_b(q + 1, B);
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-            const int k = nz - 1 - (q * kChunk + u);
-            if (k >= 0) {
-                z = fma(-A.b[u], z, A.a[u]) * A.d[u];
-                const long long c = col + nxy * k;
-                out[c] = z;
-                if (hi) {
-                    const F2Split sp = split_f2(z);
-                    hi[c] = sp.hi;
-                    lo[c] = sp.lo;
-                }
-            }
+    for (int q = 0; q < nz; ++q) {
+        cp_wait<kLineDepth - 1>();
+        const int sl = q % kLineDepth;
+        z = fma(-ring[sl][1][l], z, ring[sl][0][l]) * ring[sl][2][l];
+        const long long c = col + nxy * (nz - 1 - q);
+        out[c] = z;
+        if (hi) {
+            const F2Split sp = split_f2(z);
+            hi[c] = sp.hi;
+            lo[c] = sp.lo;
         }
-        A = B;
+        issue_b(q + kLineDepth);
     }
+    cp_wait<0>();
 }
 
 // x = 0, r = r^ = sign * b; partials of (b, b).
@@ -484,8 +487,8 @@ cudaError_t krylov_dinv(const GridGeom& g, bool mixed, const void* vals, const d
 
 static cudaError_t line_apply(const GridGeom& g, const KrylovWork& w, const double* in, double* out, float* hi,
                               float* lo, cudaStream_t st) {
-    const unsigned nb = (unsigned)(((long long)g.nx * g.ny + kLineThreads - 1) / kLineThreads);
-    k_line_apply<<<nb, kLineThreads, 0, st>>>(g, w.dinv, w.lmul, w.up, in, out, hi, lo, w.S);
+    const unsigned nb = (unsigned)(((long long)g.nx * g.ny + kApplyThreads - 1) / kApplyThreads);
+    k_line_apply<<<nb, kApplyThreads, 0, st>>>(g, w.dinv, w.lmul, w.up, in, out, hi, lo, w.S);
     return cudaGetLastError();
 }
 
