@@ -79,6 +79,27 @@ def fp64_ops_per_cell(kernel_hash: str):
         return None
 
 
+def profiled_instructions(kernel_hash: str, summary="assemble_mixed_256x256x128_instmix.md"):
+    """Warp instructions issued per cell by the assembly kernel, from the
+    committed ncu instruction-mix summary, if it was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.strip().startswith("- `"):
+                key, _, v = line.strip()[3:].partition("`:")
+                vals[key.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_hash:
+        return None
+    try:
+        return float(vals["warp_instructions_per_cell"])
+    except (KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -250,6 +271,19 @@ def run_ours(args):
     achieved = nbytes / avg_launch_s / 1e9
     khash = kernel_source_hash()
     tma = args.kernel == "tiled_tma"
+    # instruction-issue bound of the same kernel: warp instructions per cell
+    # (ncu) x cells/s against 4 issue slots per SM per clock at the sampled
+    # SM clock
+    ipc = None if tma else profiled_instructions(khash)
+    issue_roofline = None
+    if ipc is not None:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        issue_peak = 4.0 * sms * mhz * 1e6
+        issue_achieved = prob.n / (statistics.mean(launch_ms) * 1e-3) * ipc
+        issue_roofline = {"bound": "issue", "warp_instructions_per_cell": ipc, "achieved": issue_achieved / 1e12,
+                          "peak": issue_peak / 1e12, "unit": "T warp instructions/s", "frac": issue_achieved / issue_peak,
+                          "source": "ncu count in profiles/assemble_mixed_256x256x128_instmix.md"}
     kname = "k_assemble_ymarch_tma<DIAG,!CR,JAC,W=4>" if tma else "k_assemble_ymarch<float,DIAG,!CR,JAC>"
     traffic = profiled_traffic(khash, "assemble_tma_mixed_512x512x256.md" if tma else "assemble_mixed_512x512x256.md")
 
@@ -340,6 +374,7 @@ def run_ours(args):
                    "pressure_vectors": len(pres), "parallelism": f"replicas x{world}",
                    "tiling": {"rows_per_march": tiling[0], "warps_per_block": 4 if tma else tiling[1]},
                    "kernel_variant": args.kernel},
+        "issue_roofline": issue_roofline,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
                      "kernel": kname, "kernel_source_sha256_16": khash},
