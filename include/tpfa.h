@@ -171,6 +171,15 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
 int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream);
 
 /*
+ * As tpfa_set_permeability with the natural log of the permeability given:
+ * log_perm_dev holds N doubles ln k (read asynchronously on `stream`); the
+ * library forms k = exp(ln k) on the device.  This is the parameterisation
+ * of the adjoint's g_lnk (tpfa_vjp), so an optimiser over ln k can bind its
+ * iterate without any arithmetic of its own.
+ */
+int tpfa_set_log_permeability(tpfa_handle h, const double* log_perm_dev, void* stream);
+
+/*
  * Adjoint of the residual (vector-Jacobian products) at the bound state:
  *   g_p[i]   = sum_K v_K dR_K/dp_i              (= J^T v)
  *   g_lnk[i] = sum_K v_K dR_K/d(ln k_i)         (natural log)
@@ -444,25 +453,42 @@ int tpfa_destroy_ensemble(tpfa_ensemble e);
  *       to 1 when an assembled value is NaN/Inf and to 0 otherwise
  *   stream     : cudaStream_t as void*; the call is asynchronous on it
  *
- * Limits: the workspace holds, per cell, the owned transmissibilities, m^n
- * (FP64) and on the mixed path the FP32 depth (and FP32 phi0 when c_r != 0):
- * 32 bytes per cell with 10 links on the mixed path (36 with c_r != 0, so
- * about 2.09 M and 1.86 M cells) and 48 bytes on the FP64 path (about
- * 1.39 M cells).  Larger grids return TPFA_ERR_TOO_LARGE, with a message
- * giving the bytes needed, before any device work; use the handle API for
- * them.
+ * Limits: the workspace holds the error word (the first 256 bytes), then
+ * each intermediate array starting on a 256-byte boundary: the owned
+ * transmissibilities (3 with 6 links, 5 with 10; field type), on the mixed
+ * path the FP32 depth (and the FP32 phi0 when c_r != 0), and m^n (FP64).
+ * A grid is accepted exactly when
+ *     256 + sum over those arrays of align256(N * bytes per element)
+ *         <= TPFA_STATIC_WORKSPACE_BYTES,
+ * align256(x) rounding x up to a multiple of 256; tpfa_static_workspace_bytes
+ * evaluates the left-hand side.  That is about 32 bytes per cell with 10
+ * links on the mixed path (36 with c_r != 0: about 2.09 M and 1.86 M cells)
+ * and 48 bytes on the FP64 path (about 1.39 M cells).  Larger grids return
+ * TPFA_ERR_TOO_LARGE, with a message giving the bytes needed, before any
+ * device work; use the handle API for them.
  *
  * The workspace is shared by every call and keeps the last call's contents;
  * each call overwrites what it reads and clears its error word first.  Calls
  * whose GPU work overlaps (other streams or host threads without ordering)
- * race on it.  The first call on each device looks up the workspace's device
- * address with that device current and caches it; make that first call
- * before any stream capture.
+ * race on it.  Each call outside stream capture looks up the workspace's
+ * device address on the current device (cudaGetSymbolAddress) and keeps it;
+ * a call made while `stream` is being captured uses the address kept from
+ * an earlier call on that device, so make the first call on each device
+ * before any stream capture (a first call under capture returns
+ * TPFA_ERR_CUDA).
  */
 int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_params* prm, tpfa_precision prec,
                                   const double* perm_dev, const double* poro_dev, const double* depth_dev,
                                   const void* p_dev, const void* p_prev_dev, double* R_dev, void* vals_dev,
                                   double* diag64_dev, unsigned int* status_dev, void* stream);
+
+/* Bytes of the fixed workspace that tpfa_assemble_jacobian_static needs for
+ * an nx x ny x nz grid (the left-hand side of its size rule above);
+ * rock_compressible != 0 when c_r != 0.  Host-only, needs no GPU.  Returns
+ * a negative TPFA_ERR_* code for bad arguments.  The paper has no
+ * counterpart: this is a helper of the allocation-free entry point. */
+long long tpfa_static_workspace_bytes(int nx, int ny, int nz, int connectivity, tpfa_precision prec,
+                                      int rock_compressible);
 
 /* Free everything the handle owns; NULL-safe.  Synchronises the device. */
 int tpfa_destroy(tpfa_handle h);

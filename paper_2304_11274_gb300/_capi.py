@@ -77,6 +77,7 @@ SIGNATURES = [
     ("tpfa_assemble_jacobian_kernel", _I, [_VP, _I, _VP, _VP, _VP, _VP]),
     ("tpfa_assemble_jacobian_host", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("tpfa_set_permeability", _I, [_VP, _VP, _VP]),
+    ("tpfa_set_log_permeability", _I, [_VP, _VP, _VP]),
     ("tpfa_vjp", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_vjp_kernel", _I, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     ("tpfa_jvp", _I, [_VP, _VP, _VP, _VP, _VP]),
@@ -108,6 +109,7 @@ SIGNATURES = [
     ("tpfa_ensemble_autotune", _I, [_VP, ctypes.c_char_p, _VP]),
     ("tpfa_destroy_ensemble", _I, [_VP]),
     ("tpfa_assemble_jacobian_static", _I, [_I, _I, _I, ctypes.POINTER(TPFAParams), _I] + [_VP] * 10),
+    ("tpfa_static_workspace_bytes", _LL, [_I, _I, _I, _I, _I, _I]),
     ("tpfa_destroy", _I, [_VP]),
     ("tpfa_last_error_string", ctypes.c_char_p, []),
     ("tpfa_version", _I, []),

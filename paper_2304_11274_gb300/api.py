@@ -159,6 +159,15 @@ class Grid:
         check(self.lib.tpfa_set_permeability(self.handle, _ptr(k), _stream(stream)))
         self._perm = k  # read asynchronously: keep it alive
 
+    def set_log_permeability(self, log_k, stream=None):
+        """Replace ln k (natural log of m^2); the library forms k = exp(ln k)
+        and recomputes the transmissibilities on the device."""
+        lk = _dev_f64(log_k, self.device)
+        if lk.numel() != self.n:
+            raise ValueError(f"expected {self.n} values, got {lk.numel()}")
+        check(self.lib.tpfa_set_log_permeability(self.handle, _ptr(lk), _stream(stream)))
+        self._perm = lk  # read asynchronously: keep it alive
+
     def vjp(self, v, want_lnk=True, kernel="auto", stream=None):
         """(g_p, g_lnk) = (v^T dR/dp, v^T dR/d ln k) at the bound state, FP64."""
         v = _dev_f64(v, self.device)
@@ -450,7 +459,7 @@ class TPFAResidual(torch.autograd.Function):
 def _apply_log_k(grid, log_k):
     # Always re-applied: a tensor's address and version do not identify its
     # contents (the caching allocator reuses addresses).
-    grid.set_permeability(torch.exp(log_k.detach().to(torch.float64)))
+    grid.set_log_permeability(log_k.detach())
 
 
 def residual(grid, p, log_k):

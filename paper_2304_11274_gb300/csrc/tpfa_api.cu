@@ -10,6 +10,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
 #include <string>
 #include <utility>
 #include <vector>
@@ -74,6 +76,19 @@ struct DeviceGuard {
 namespace tpfa {
 // Error reporting for entry points defined in other translation units.
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+cudaError_t ensure_smem_limit(const void* func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;  // (kernel, device) pairs whose limit is raised
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({func, dev})) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert({func, dev});
+    return e;
+}
 }  // namespace tpfa
 
 struct tpfa_grid {
@@ -190,7 +205,10 @@ AsmFields<Real> fields_of(const tpfa_grid* h) {
     f.pn = static_cast<const Real*>(h->pn);
     f.mn = h->mn;
     f.z = static_cast<const Real*>(h->z);
-    f.phi0 = static_cast<const Real*>(h->phi0_r);
+    // phi0 in the field type exists only when c_r != 0 (the only case that
+    // reads it); otherwise the pointer names the depth array, so that no
+    // kernel ever receives a NULL field pointer
+    f.phi0 = static_cast<const Real*>(h->phi0_r ? h->phi0_r : h->z);
     f.Tx = static_cast<const Real*>(h->T[0]);
     f.Ty = static_cast<const Real*>(h->T[1]);
     f.Tz = static_cast<const Real*>(h->T[2]);
@@ -702,7 +720,8 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
     return TPFA_OK;
 }
 
-int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream) {
+namespace {
+int set_perm(tpfa_handle h, const double* perm_dev, void* stream, bool log_k) {
     int rc = check_handle(h);
     if (rc) return rc;
     if (!perm_dev) return fail(TPFA_ERR_INVALID_ARG, "perm must be non-NULL");
@@ -711,15 +730,24 @@ int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream) {
     cudaError_t e;
     if (h->prec == TPFA_MIXED) {
         e = launch_transmissibility_f32(h->geom, h->sp, perm_dev, (float*)h->T[0], (float*)h->T[1], (float*)h->T[2],
-                                        (float*)h->T[3], (float*)h->T[4], st);
-        if (e == cudaSuccess) e = launch_store_perm_f32(perm_dev, (float*)h->kperm, h->N, st);
+                                        (float*)h->T[3], (float*)h->T[4], st, log_k);
+        if (e == cudaSuccess) e = launch_store_perm_f32(perm_dev, (float*)h->kperm, h->N, st, log_k);
     } else {
         e = launch_transmissibility_f64(h->geom, h->sp, perm_dev, (double*)h->T[0], (double*)h->T[1],
-                                        (double*)h->T[2], (double*)h->T[3], (double*)h->T[4], st);
-        if (e == cudaSuccess) e = launch_store_perm_f64(perm_dev, (double*)h->kperm, h->N, st);
+                                        (double*)h->T[2], (double*)h->T[3], (double*)h->T[4], st, log_k);
+        if (e == cudaSuccess) e = launch_store_perm_f64(perm_dev, (double*)h->kperm, h->N, st, log_k);
     }
     if (e != cudaSuccess) return cuda_fail(e, "set_permeability launch");
     return TPFA_OK;
+}
+}  // namespace
+
+int tpfa_set_permeability(tpfa_handle h, const double* perm_dev, void* stream) {
+    return set_perm(h, perm_dev, stream, false);
+}
+
+int tpfa_set_log_permeability(tpfa_handle h, const double* log_perm_dev, void* stream) {
+    return set_perm(h, log_perm_dev, stream, true);
 }
 
 int tpfa_vjp_kernel(tpfa_handle h, tpfa_kernel kern, const double* v_dev, double* g_p_dev, double* g_lnk_dev,

@@ -53,13 +53,8 @@ static cudaError_t launch_ymarch_w(const GridGeom& g, const typename PhysOf<Real
                                    const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int k0, int k1,
                                    cudaStream_t st) {
     constexpr int smem = ymarch_smem_bytes<Real, W>();
-    static bool attr_set = false;  // per instantiation; the attribute is per function
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_assemble_ymarch<Real, DIAG, CRK, JAC, W>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(&k_assemble_ymarch<Real, DIAG, CRK, JAC, W>), smem);
+    if (e != cudaSuccess) return e;
     dim3 block(32, W, 1);
     dim3 grid((g.nx + 31) / 32, (g.ny + JY - 1) / JY, (k1 - k0 + W - 1) / W);
     k_assemble_ymarch<Real, DIAG, CRK, JAC, W><<<grid, block, smem, st>>>(g, q, f, o, JY, k0 / W);
@@ -109,13 +104,8 @@ static cudaError_t launch_tma_t(const GridGeom& g, const PhysF& q, const AsmFiel
                                 const TmaMaps& maps, int JY, int k0, int k1, cudaStream_t st) {
     constexpr int W = kTmaWarps;
     constexpr int smem = ymarch_tma_smem_bytes<W, YMarch<float, DIAG, CRK, JAC, W>::TRING>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_assemble_ymarch_tma<DIAG, CRK, JAC, W>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(&k_assemble_ymarch_tma<DIAG, CRK, JAC, W>), smem);
+    if (e != cudaSuccess) return e;
     dim3 block(32, W, 1);
     dim3 grid((g.nx + 32 * W - 1) / (32 * W), (g.ny + JY - 1) / JY, k1 - k0);
     k_assemble_ymarch_tma<DIAG, CRK, JAC, W><<<grid, block, smem, st>>>(g, q, f, o, maps, JY, k0);

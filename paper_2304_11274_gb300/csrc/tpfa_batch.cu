@@ -56,13 +56,9 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
 template <bool DIAG, bool CRK, int W>
 cudaError_t config(const void** func, int* smem_bytes) {
     constexpr int smem = ymarch_smem_bytes<float, W>();
-    static bool attr_set = false;
     const void* f = reinterpret_cast<const void*>(&k_assemble_batch<DIAG, CRK, W>);
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const cudaError_t e = ensure_smem_limit(f, smem);
+    if (e != cudaSuccess) return e;
     *func = f;
     *smem_bytes = smem;
     return cudaSuccess;

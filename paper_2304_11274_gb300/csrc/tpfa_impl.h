@@ -43,12 +43,13 @@ struct SetupPhys {
 };
 // Owned transmissibilities from permeability, computed in FP64 and stored as
 // `Real` (float or double).  Tpp/Tmp may be null with 6-point connectivity.
+// With log_k the array holds ln k and k = exp(ln k) is formed per read.
 cudaError_t launch_transmissibility_f32(const GridGeom& g, const SetupPhys& s, const double* perm,
                                         float* Tx, float* Ty, float* Tz, float* Tpp, float* Tmp,
-                                        cudaStream_t st);
+                                        cudaStream_t st, bool log_k = false);
 cudaError_t launch_transmissibility_f64(const GridGeom& g, const SetupPhys& s, const double* perm,
                                         double* Tx, double* Ty, double* Tz, double* Tpp, double* Tmp,
-                                        cudaStream_t st);
+                                        cudaStream_t st, bool log_k = false);
 cudaError_t launch_convert_f32(const double* in, float* out, long long n, cudaStream_t st);
 cudaError_t launch_copy_f64(const double* in, double* out, long long n, cudaStream_t st);
 // m^n = (V/dt) phi(p^n) rho(p^n) in FP64 from p^n of either field type.
@@ -73,8 +74,9 @@ cudaError_t launch_jvp_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, 
                              cudaStream_t st);
 cudaError_t launch_jvp_fp64(const GridGeom& g, const PhysD& q, bool crk, const AsmFields<double>& f, const double* w,
                             double* Jw, double* R, unsigned int* status, cudaStream_t st);
-cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st);
-cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st);
+// k in the path's precision (the adjoint's copy), from k or (log_k) ln k.
+cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st, bool log_k = false);
+cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st, bool log_k = false);
 
 // Preconditioned BiCGStab (tpfa_krylov.cu).  The scalars live on the
 // device; the host polls them.
@@ -112,6 +114,12 @@ cudaError_t launch_mesh_fp64(const MeshFields<double>& f, long long n, const Phy
 
 // Sets the thread-local message of tpfa_last_error_string and returns code.
 int report_error(int code, const char* msg);
+
+// Raises `func`'s dynamic shared-memory limit to `bytes` in the current
+// device's context.  The attribute belongs to the function in one context,
+// so it is set once per (function, device) pair; the record of pairs done
+// is guarded by a mutex, so host threads may launch concurrently.
+cudaError_t ensure_smem_limit(const void* func, int bytes);
 
 // CSR pattern (row_ptr int64 N+1, col_idx int32 nnz).
 cudaError_t launch_pattern(const GridGeom& g, long long* row_ptr, int* col_idx, cudaStream_t st);

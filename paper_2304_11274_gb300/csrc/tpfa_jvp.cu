@@ -206,13 +206,8 @@ template <bool DIAG, bool CRK, int W>
 cudaError_t launch_jvp_ymarch_w(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const double* w,
                                 double* Jw, double* R, unsigned int* status, int JY, cudaStream_t st) {
     constexpr int smem = jvp_smem_bytes<W>();
-    static bool attr = false;  // per-process: the attribute is set once per kernel instance
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_jvp_ymarch<DIAG, CRK, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(&k_jvp_ymarch<DIAG, CRK, W>), smem);
+    if (e != cudaSuccess) return e;
     dim3 block(32, W, 1);
     dim3 grid((g.nx + 31) / 32, (g.ny + JY - 1) / JY, (g.nz + W - 1) / W);
     AsmOut<float> o{R, nullptr, nullptr, status};

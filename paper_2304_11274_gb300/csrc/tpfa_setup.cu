@@ -30,7 +30,14 @@ struct Geo {
     double ax, ay, az, ad;  // area / distance of x, y, z faces and of an in-plane diagonal
 };
 
-template <typename Real>
+// Permeability of cell c: the stored value, or exp of the stored natural
+// log (the adjoint's parameterisation, k = exp(ln k)).
+template <bool LOG>
+__device__ __forceinline__ double perm_at(const double* __restrict__ perm, long long c) {
+    return LOG ? exp(perm[c]) : perm[c];
+}
+
+template <typename Real, bool LOG>
 __global__ void k_trans(GridGeom g, Geo geo, const double* __restrict__ perm, Real* Tx, Real* Ty, Real* Tz,
                         Real* Tpp, Real* Tmp) {
     const long long nx = g.nx, nxy = nx * g.ny, N = nxy * g.nz;
@@ -41,17 +48,24 @@ __global__ void k_trans(GridGeom g, Geo geo, const double* __restrict__ perm, Re
         const int i = (int)(c - k * nxy - j * nx);
         // neighbour indices fall back to c itself where the link does not
         // exist, so every address formed is inside perm
-        const double kc = perm[c];
+        const double kc = perm_at<LOG>(perm, c);
         const bool xp = i + 1 < g.nx, yp = j + 1 < g.ny, zp = k + 1 < g.nz;
-        Tx[c] = (Real)(xp ? two_point(kc, perm[xp ? c + 1 : c], geo.ax) : 0.0);
-        Ty[c] = (Real)(yp ? two_point(kc, perm[yp ? c + nx : c], geo.ay) : 0.0);
-        Tz[c] = (Real)(zp ? two_point(kc, perm[zp ? c + nxy : c], geo.az) : 0.0);
+        Tx[c] = (Real)(xp ? two_point(kc, perm_at<LOG>(perm, xp ? c + 1 : c), geo.ax) : 0.0);
+        Ty[c] = (Real)(yp ? two_point(kc, perm_at<LOG>(perm, yp ? c + nx : c), geo.ay) : 0.0);
+        Tz[c] = (Real)(zp ? two_point(kc, perm_at<LOG>(perm, zp ? c + nxy : c), geo.az) : 0.0);
         if (g.diag) {
             const bool pp = yp && xp, mp = yp && i > 0;
-            Tpp[c] = (Real)(pp ? two_point(kc, perm[pp ? c + nx + 1 : c], geo.ad) : 0.0);
-            Tmp[c] = (Real)(mp ? two_point(kc, perm[mp ? c + nx - 1 : c], geo.ad) : 0.0);
+            Tpp[c] = (Real)(pp ? two_point(kc, perm_at<LOG>(perm, pp ? c + nx + 1 : c), geo.ad) : 0.0);
+            Tmp[c] = (Real)(mp ? two_point(kc, perm_at<LOG>(perm, mp ? c + nx - 1 : c), geo.ad) : 0.0);
         }
     }
+}
+
+// k in the path's precision for the adjoint, from k or from ln k.
+template <typename Real, bool LOG>
+__global__ void k_store_perm(const double* __restrict__ perm, Real* out, long long n) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        out[c] = (Real)perm_at<LOG>(perm, c);
 }
 
 Geo make_geo(const SetupPhys& s) {
@@ -120,16 +134,31 @@ __global__ void k_pattern(GridGeom g, long long* row_ptr, int* col_idx) {
 }  // namespace
 
 cudaError_t launch_transmissibility_f32(const GridGeom& g, const SetupPhys& s, const double* perm, float* Tx,
-                                        float* Ty, float* Tz, float* Tpp, float* Tmp, cudaStream_t st) {
+                                        float* Ty, float* Tz, float* Tpp, float* Tmp, cudaStream_t st, bool log_k) {
     const long long N = (long long)g.nx * g.ny * g.nz;
-    k_trans<float><<<blocks_for(N), kThreads, 0, st>>>(g, make_geo(s), perm, Tx, Ty, Tz, Tpp, Tmp);
+    if (log_k) k_trans<float, true><<<blocks_for(N), kThreads, 0, st>>>(g, make_geo(s), perm, Tx, Ty, Tz, Tpp, Tmp);
+    else k_trans<float, false><<<blocks_for(N), kThreads, 0, st>>>(g, make_geo(s), perm, Tx, Ty, Tz, Tpp, Tmp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_transmissibility_f64(const GridGeom& g, const SetupPhys& s, const double* perm, double* Tx,
-                                        double* Ty, double* Tz, double* Tpp, double* Tmp, cudaStream_t st) {
+                                        double* Ty, double* Tz, double* Tpp, double* Tmp, cudaStream_t st,
+                                        bool log_k) {
     const long long N = (long long)g.nx * g.ny * g.nz;
-    k_trans<double><<<blocks_for(N), kThreads, 0, st>>>(g, make_geo(s), perm, Tx, Ty, Tz, Tpp, Tmp);
+    if (log_k) k_trans<double, true><<<blocks_for(N), kThreads, 0, st>>>(g, make_geo(s), perm, Tx, Ty, Tz, Tpp, Tmp);
+    else k_trans<double, false><<<blocks_for(N), kThreads, 0, st>>>(g, make_geo(s), perm, Tx, Ty, Tz, Tpp, Tmp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st, bool log_k) {
+    if (log_k) k_store_perm<float, true><<<blocks_for(n), kThreads, 0, st>>>(perm, out, n);
+    else k_store_perm<float, false><<<blocks_for(n), kThreads, 0, st>>>(perm, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st, bool log_k) {
+    if (log_k) k_store_perm<double, true><<<blocks_for(n), kThreads, 0, st>>>(perm, out, n);
+    else k_store_perm<double, false><<<blocks_for(n), kThreads, 0, st>>>(perm, out, n);
     return cudaGetLastError();
 }
 

@@ -16,9 +16,14 @@
 // whose work overlaps on the GPU (different streams, or different host
 // threads, without ordering between them) race on the workspace.
 //
-// Host code cannot use the array's name as a device address, so the first
-// call on each device asks the runtime for the array's device address
-// (cudaGetSymbolAddress, with that device current) and caches it.
+// Host code cannot use the array's name as a device address, so each call
+// asks the runtime for the array's device address on the current device
+// (cudaGetSymbolAddress) and keeps it per device.  While the stream is being
+// captured into a CUDA graph the kept address is used instead of a new
+// query, so the first call on a device must come before any capture.  A
+// call outside capture always queries afresh: after cudaDeviceReset the
+// library's module is loaded again, possibly elsewhere, and an address kept
+// from before would point at freed memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -40,12 +45,17 @@ static __device__ __align__(256) unsigned char g_workspace[kWorkspaceBytes];
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
 
-// Device address of g_workspace on the current device (set up once per device).
-cudaError_t workspace_address(int dev, unsigned char** out) {
+// Device address of g_workspace on device `dev` (current): queried on every
+// call outside stream capture, the kept one during capture.
+cudaError_t workspace_address(int dev, cudaStream_t st, unsigned char** out) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_addr[dev]) {
+        if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;  // no address kept yet
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_workspace);
+        e = cudaGetSymbolAddress(&p, g_workspace);
         if (e != cudaSuccess) return e;
         g_addr[dev] = p;
     }
@@ -54,6 +64,35 @@ cudaError_t workspace_address(int dev, unsigned char** out) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout: the error word in the first 256 bytes, then each array
+// from a 256-byte boundary: the owned transmissibilities (3 or 5, field
+// type), on the mixed path the FP32 depth (and the FP32 phi0 when c_r != 0),
+// then m^n (FP64).  Returns the bytes used.
+struct Layout {
+    size_t T[5] = {0, 0, 0, 0, 0};
+    size_t z = 0, phi = 0, mn = 0;
+};
+size_t layout(long long N, int connectivity, bool mixed, bool crk, Layout* L) {
+    const size_t rs = mixed ? sizeof(float) : sizeof(double);
+    const int nT = connectivity == 10 ? 5 : 3;
+    size_t off = 256;
+    for (int t = 0; t < nT; ++t) {
+        L->T[t] = off;
+        off += align256(rs * (size_t)N);
+    }
+    if (mixed) {
+        L->z = off;
+        off += align256(rs * (size_t)N);
+        if (crk) {
+            L->phi = off;
+            off += align256(rs * (size_t)N);
+        }
+    }
+    L->mn = off;
+    off += align256(sizeof(double) * (size_t)N);
+    return off;
+}
 
 }  // namespace
 
@@ -72,45 +111,29 @@ extern "C" int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_
     const long long N = (long long)nx * ny * nz;
     if (N >= (1LL << 31)) return report_error(TPFA_ERR_TOO_LARGE, "static assembly: N exceeds 2^31 - 1");
 
-    // Workspace layout: error word, owned transmissibilities, and for the
-    // mixed path the FP32 depth (and FP32 phi0 when c_r != 0); then m^n.
     const bool mixed = prec == TPFA_MIXED;
     const bool crk = prm->c_r != 0.0;
-    const size_t rs = mixed ? sizeof(float) : sizeof(double);
-    const int nT = prm->connectivity == 10 ? 5 : 3;
-    size_t off = 256;  // the error word sits in the first 256 bytes
-    size_t offT[5] = {0, 0, 0, 0, 0};
-    for (int t = 0; t < nT; ++t) {
-        offT[t] = off;
-        off += align256(rs * (size_t)N);
-    }
-    size_t offZ = 0, offPhi = 0;
-    if (mixed) {
-        offZ = off;
-        off += align256(rs * (size_t)N);
-        if (crk) {
-            offPhi = off;
-            off += align256(rs * (size_t)N);
-        }
-    }
-    const size_t offM = off;
-    off += align256(sizeof(double) * (size_t)N);
-    if (off > kWorkspaceBytes) {
+    Layout L;
+    const size_t need = layout(N, prm->connectivity, mixed, crk, &L);
+    if (need > kWorkspaceBytes) {
         char msg[200];
         snprintf(msg, sizeof msg,
                  "static assembly: a %d x %d x %d grid needs %zu bytes of workspace, more than the fixed %zu "
-                 "(use the handle API for larger grids)", nx, ny, nz, off, kWorkspaceBytes);
+                 "(use the handle API for larger grids)", nx, ny, nz, need, kWorkspaceBytes);
         return report_error(TPFA_ERR_TOO_LARGE, msg);
     }
+    const int nT = prm->connectivity == 10 ? 5 : 3;
+    const size_t* offT = L.T;
+    const size_t offZ = L.z, offPhi = L.phi, offM = L.mn;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return report_error(TPFA_ERR_CUDA, "static assembly: no usable current device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* ws = nullptr;
-    cudaError_t ea = workspace_address(dev, &ws);
+    cudaError_t ea = workspace_address(dev, st, &ws);
     if (ea != cudaSuccess) return report_error(TPFA_ERR_CUDA, cudaGetErrorString(ea));
 
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned int* status = status_dev ? status_dev : reinterpret_cast<unsigned int*>(ws);
     const GridGeom g{nx, ny, nz, prm->connectivity == 10 ? 1 : 0};
     const double V_dt = prm->dx * prm->dy * prm->dz / prm->dt;
@@ -122,7 +145,7 @@ extern "C" int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
     if (mixed) {
         float* z = reinterpret_cast<float*>(ws + offZ);
-        float* phi = crk ? reinterpret_cast<float*>(ws + offPhi) : nullptr;
+        float* phi = crk ? reinterpret_cast<float*>(ws + offPhi) : z;  // read only when c_r != 0; never NULL
         if (e == cudaSuccess)
             e = launch_transmissibility_f32(g, sp, perm_dev, (float*)T[0], (float*)T[1], (float*)T[2], (float*)T[3],
                                             (float*)T[4], st);
@@ -154,4 +177,15 @@ extern "C" int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_
     }
     if (e != cudaSuccess) return report_error(TPFA_ERR_CUDA, cudaGetErrorString(e));
     return TPFA_OK;
+}
+
+extern "C" long long tpfa_static_workspace_bytes(int nx, int ny, int nz, int connectivity, tpfa_precision prec,
+                                                 int rock_compressible) {
+    if (nx < 1 || ny < 1 || nz < 1 || (connectivity != 6 && connectivity != 10) ||
+        (prec != TPFA_FP64 && prec != TPFA_MIXED))
+        return report_error(TPFA_ERR_INVALID_ARG, "static workspace size: bad grid size, connectivity or precision");
+    const long long N = (long long)nx * ny * nz;
+    if (N >= (1LL << 31)) return report_error(TPFA_ERR_TOO_LARGE, "static workspace size: N exceeds 2^31 - 1");
+    Layout L;
+    return (long long)layout(N, connectivity, prec == TPFA_MIXED, rock_compressible != 0, &L);
 }

@@ -307,13 +307,8 @@ cudaError_t launch_vjp_ymarch_w(const GridGeom& g, const PhysF& q, const AsmFiel
                                 const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
                                 unsigned int* status, int JY, cudaStream_t st) {
     constexpr int smem = vjp_smem_bytes<W>();
-    static bool attr = false;  // per-process: the attribute is set once per kernel instance
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_vjp_ymarch<DIAG, CRK, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(&k_vjp_ymarch<DIAG, CRK, W>), smem);
+    if (e != cudaSuccess) return e;
     dim3 block(32, W, 1);
     dim3 grid((g.nx + 31) / 32, (g.ny + JY - 1) / JY, (g.nz + W - 1) / W);
     AsmOut<float> o{nullptr, nullptr, nullptr, status};
@@ -327,13 +322,6 @@ cudaError_t launch_vjp_ymarch_t(const GridGeom& g, const PhysF& q, const AsmFiel
                                 unsigned int* status, int JY, int W, cudaStream_t st) {
     if (W == 8) return launch_vjp_ymarch_w<DIAG, CRK, 8>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
     return launch_vjp_ymarch_w<DIAG, CRK, 4>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
-}
-
-// k stored in the path's precision for the adjoint.
-template <typename Real>
-__global__ void k_store_perm(const double* __restrict__ perm, Real* out, long long n) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-        out[c] = (Real)perm[c];
 }
 
 }  // namespace
@@ -371,18 +359,6 @@ cudaError_t launch_vjp_fp64(const GridGeom& g, const PhysD& q, bool crk, const A
                             const double* kperm, const double* v, double* g_p, double* g_lnk,
                             unsigned int* status, cudaStream_t st) {
     return launch_vjp_t<double>(g, q, crk, f, kperm, v, g_p, g_lnk, status, st);
-}
-
-cudaError_t launch_store_perm_f32(const double* perm, float* out, long long n, cudaStream_t st) {
-    const long long b = (n + 255) / 256;
-    k_store_perm<float><<<(unsigned)(b < (1LL << 30) ? (b > 0 ? b : 1) : (1LL << 30)), 256, 0, st>>>(perm, out, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_store_perm_f64(const double* perm, double* out, long long n, cudaStream_t st) {
-    const long long b = (n + 255) / 256;
-    k_store_perm<double><<<(unsigned)(b < (1LL << 30) ? (b > 0 ? b : 1) : (1LL << 30)), 256, 0, st>>>(perm, out, n);
-    return cudaGetLastError();
 }
 
 }  // namespace tpfa
