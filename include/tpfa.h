@@ -68,7 +68,8 @@ typedef enum {
  * link and sum every row in the same order with the same roundings, so they
  * give bit-identical results. */
 typedef enum {
-    TPFA_KERNEL_AUTO = 0,  /* the library's choice (currently TILED) */
+    TPFA_KERNEL_AUTO = 0,  /* the library's choice: TILED2 for the fused residual
+                              + Jacobian of TPFA_MIXED grids it accepts, else TILED */
     TPFA_KERNEL_NAIVE = 1, /* one thread per cell, every neighbour read from
                               global memory: the correctness baseline */
     TPFA_KERNEL_TILED = 2, /* a warp per 32-cell x-segment of a z-plane,
@@ -76,7 +77,7 @@ typedef enum {
                               registers and x-neighbours exchanged by warp
                               shuffles; each lane prefetches its row inputs
                               with cp.async */
-    TPFA_KERNEL_TILED_TMA = 3 /* TILED with 4 warps per block on 4
+    TPFA_KERNEL_TILED_TMA = 3, /* TILED with 4 warps per block on 4
                               consecutive x-segments of one plane, each row's
                               inputs fetched for the whole block as a few
                               boxes by the tensor memory accelerator
@@ -84,6 +85,13 @@ typedef enum {
                               assembly calls only, TPFA_MIXED, nx a multiple
                               of 4 and p, p^n 16-byte aligned, else
                               TPFA_ERR_INVALID_ARG */
+    TPFA_KERNEL_TILED2 = 4 /* TILED with two adjacent cells per lane (64-cell
+                              x-segments): each link is one half of a paired
+                              FP32 instruction and every input moves as one
+                              8-byte copy per lane for two cells; fused
+                              residual + Jacobian of TPFA_MIXED with nx even
+                              and 8-byte aligned fields (16-byte m^n), else
+                              the call runs TILED */
 } tpfa_kernel;
 
 typedef struct {

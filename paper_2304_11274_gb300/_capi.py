@@ -24,7 +24,7 @@ ERRORS = {
     -9: "TPFA_ERR_NO_CONVERGENCE",
 }
 TPFA_FP64, TPFA_MIXED = 0, 1
-KERNELS = {"auto": 0, "naive": 1, "tiled": 2, "tiled_tma": 3}
+KERNELS = {"auto": 0, "naive": 1, "tiled": 2, "tiled_tma": 3, "tiled2": 4}
 PRECONDITIONERS = {"zline": 0, "jacobi": 1}
 
 

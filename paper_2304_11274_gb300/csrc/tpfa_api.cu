@@ -236,11 +236,13 @@ bool tma_ready(tpfa_grid* h) {
     return h->tm_state;
 }
 
-// The library's choice of assembly kernel: the per-lane march.  (The TMA
-// march gives the same bits but measured 8 % slower on the 512 x 512 x 256
-// workload: its row waits stall where the per-lane prefetch does not, and
-// it saves no instructions.)
-AsmKernel auto_kernel(tpfa_grid*) { return AsmKernel::YMarch; }
+// The library's choice of assembly kernel: the march with two cells per lane
+// (the dispatch runs the one-cell march where that one does not apply:
+// residual-only calls, the FP64 path, odd nx, fields not pair-aligned).
+// (The TMA march gives the same bits but measured 8 % slower than the
+// one-cell march on the 512 x 512 x 256 workload: its row waits stall where
+// the per-lane prefetch does not, and it saves no instructions.)
+AsmKernel auto_kernel(tpfa_grid*) { return AsmKernel::XMarch; }
 
 int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st, int k0 = 0,
            int k1 = -1) {
@@ -622,6 +624,7 @@ int tpfa_assemble_jacobian_kernel(tpfa_handle h, tpfa_kernel kern, double* R_dev
         case TPFA_KERNEL_AUTO: k = auto_kernel(h); break;
         case TPFA_KERNEL_TILED: k = AsmKernel::YMarch; break;
         case TPFA_KERNEL_TILED_TMA: k = AsmKernel::YMarchTma; break;
+        case TPFA_KERNEL_TILED2: k = AsmKernel::XMarch; break;
         case TPFA_KERNEL_NAIVE: k = AsmKernel::Naive; break;
         default: return fail(TPFA_ERR_INVALID_ARG, "bad kernel variant %d", (int)kern);
     }

@@ -23,6 +23,7 @@
 #include "tpfa_impl.h"
 #include "tpfa_row.cuh"
 #include "tpfa_ymarch.cuh"
+#include "tpfa_xmarch.cuh"
 
 namespace tpfa {
 
@@ -69,6 +70,47 @@ static cudaError_t launch_ymarch_t(const GridGeom& g, const typename PhysOf<Real
     return launch_ymarch_w<Real, DIAG, CRK, JAC, 4>(g, q, f, o, JY, k0, k1, st);
 }
 
+// ------------------------------------------------------------------ two cells per lane
+
+template <bool DIAG, bool CRK, int W, bool FAST>
+static cudaError_t launch_xmarch_f(const GridGeom& g, const PhysF& q, const AsmFields<float>& f,
+                                   const AsmOut<float>& o, int JY, int k0, int k1, cudaStream_t st) {
+    constexpr int smem = xmarch_smem_bytes<DIAG, CRK, W>();
+    const cudaError_t e =
+        ensure_smem_limit(reinterpret_cast<const void*>(&k_assemble_xmarch<DIAG, CRK, W, FAST>), smem);
+    if (e != cudaSuccess) return e;
+    dim3 block(32, W, 1);
+    dim3 grid((g.nx + 63) / 64, (g.ny + JY - 1) / JY, (k1 - k0 + W - 1) / W);
+    k_assemble_xmarch<DIAG, CRK, W, FAST><<<grid, block, smem, st>>>(g, q, f, o, JY, k0 / W);
+    return cudaGetLastError();
+}
+
+// FAST: R and diag64 given, and R, diag64 and vals 16-byte aligned.
+template <bool DIAG, bool CRK, int W>
+static cudaError_t launch_xmarch_w(const GridGeom& g, const PhysF& q, const AsmFields<float>& f,
+                                   const AsmOut<float>& o, int JY, int k0, int k1, cudaStream_t st) {
+    const bool fast = o.R && o.diag64 &&
+                      ((reinterpret_cast<uintptr_t>(o.R) | reinterpret_cast<uintptr_t>(o.diag64) |
+                        reinterpret_cast<uintptr_t>(o.vals)) & 15u) == 0;
+    if (fast) return launch_xmarch_f<DIAG, CRK, W, true>(g, q, f, o, JY, k0, k1, st);
+    return launch_xmarch_f<DIAG, CRK, W, false>(g, q, f, o, JY, k0, k1, st);
+}
+
+template <bool DIAG, bool CRK>
+static cudaError_t launch_xmarch_t(const GridGeom& g, const PhysF& q, const AsmFields<float>& f,
+                                   const AsmOut<float>& o, int JY, int W, int k0, int k1, cudaStream_t st) {
+    if (W == 8) return launch_xmarch_w<DIAG, CRK, 8>(g, q, f, o, JY, k0, k1, st);
+    return launch_xmarch_w<DIAG, CRK, 4>(g, q, f, o, JY, k0, k1, st);
+}
+
+static bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+bool xmarch_ok(const GridGeom& g, const AsmFields<float>& f) {
+    return g.nx % 2 == 0 && aligned_to(f.p, 8) && aligned_to(f.pn, 8) && aligned_to(f.z, 8) &&
+           aligned_to(f.phi0, 8) && aligned_to(f.Tx, 8) && aligned_to(f.Ty, 8) && aligned_to(f.Tz, 8) &&
+           aligned_to(f.Tpp, 8) && aligned_to(f.Tmp, 8) && aligned_to(f.mn, 16);
+}
+
 template <typename Real>
 static cudaError_t dispatch(AsmKernel kern, const GridGeom& g, const typename PhysOf<Real>::type& q,
                             bool crk, const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int W, int k0,
@@ -79,6 +121,17 @@ static cudaError_t dispatch(AsmKernel kern, const GridGeom& g, const typename Ph
     if (kern == AsmKernel::Naive) {
         if (crk) return jac ? launch_naive_t<Real, true, true>(g, q, f, o, st) : launch_naive_t<Real, true, false>(g, q, f, o, st);
         return jac ? launch_naive_t<Real, false, true>(g, q, f, o, st) : launch_naive_t<Real, false, false>(g, q, f, o, st);
+    }
+    if constexpr (sizeof(Real) == 4) {
+        // two cells per lane: the mixed path's fused R + J on grids with nx even
+        // and pair-aligned fields; otherwise (and for residual-only calls) the
+        // one-cell march
+        if (kern == AsmKernel::XMarch && jac && xmarch_ok(g, f)) {
+            if (g.diag) return crk ? launch_xmarch_t<true, true>(g, q, f, o, JY, W, k0, k1, st)
+                                   : launch_xmarch_t<true, false>(g, q, f, o, JY, W, k0, k1, st);
+            return crk ? launch_xmarch_t<false, true>(g, q, f, o, JY, W, k0, k1, st)
+                       : launch_xmarch_t<false, false>(g, q, f, o, JY, W, k0, k1, st);
+        }
     }
     if (g.diag) {
         if (crk) return jac ? launch_ymarch_t<Real, true, true, true>(g, q, f, o, JY, W, k0, k1, st)

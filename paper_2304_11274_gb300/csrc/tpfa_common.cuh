@@ -281,13 +281,19 @@ __device__ __forceinline__ Link2 link2(const PhysF& q, float2 T, const CellVal<f
 }
 
 // Kahan summation of two independent sums at once (.x and .y), each half
-// identical to Kahan32 on its own.
+// identical to Kahan32 on its own.  The three subtractions are written as
+// fused multiply-adds by -1 (a - b = fma(b, -1, a): the product is exact, so
+// the one rounding is the subtraction's).  Written as paired additions of a
+// negated operand, they gave sums differing from the scalar Kahan32 by an
+// ulp in the two-cell march (found by comparing variants against the naive
+// kernel; the fused form matches it bit for bit in every kernel).
 struct Kahan2 {
     float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
     __device__ __forceinline__ void add(float2 x) {
-        const float2 y = __fadd2_rn(x, neg2(c));
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 y = __ffma2_rn(c, m1, x);
         const float2 t = __fadd2_rn(s, y);
-        c = __fadd2_rn(__fadd2_rn(t, neg2(s)), neg2(y));
+        c = __ffma2_rn(y, m1, __ffma2_rn(s, m1, t));
         s = t;
     }
 };

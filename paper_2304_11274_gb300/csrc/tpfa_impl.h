@@ -13,7 +13,7 @@ namespace tpfa {
 struct PhysF;
 struct PhysD;
 
-enum class AsmKernel { Naive, YMarch, YMarchTma };
+enum class AsmKernel { Naive, YMarch, YMarchTma, XMarch };
 
 // JY: rows per warp march; W: warps (z-planes) per block, 4 or 8.  The tiled
 // kernel may be restricted to the planes [k0, k1) (k0 a multiple of W; rows

@@ -138,3 +138,26 @@ def tie_sweep_problem(precision, conn=10):
     perm = np.full(nx * ny * nz, 1e-13)
     poro = rng.uniform(0.1, 0.3, nx * ny * nz)
     return synth.Problem(nx, ny, nz, phys, perm, poro, depth, p, p.copy())
+
+
+def tie_pairs_problem(precision, conn=10, shape=(130, 37, 5), seed=31, frac=0.15):
+    """Exact ties dPhi == 0 on in-plane links of every direction: a random
+    problem in which a fraction of the cells take the pressure of one of
+    their in-plane neighbours (x, y or diagonal, chosen at random).  Both
+    cells of such a pair lie in one plane (same depth), so the link's dPhi
+    is exactly zero in either precision.  The pairs fall inside a lane's two
+    cells, across lanes and across segments alike."""
+    prob = synth.make_problem(*shape, seed=seed, connectivity=conn)
+    if precision == "mixed":
+        prob = synth.round_to_f32(prob)
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed + 1)
+    p = prob.p.reshape(nz, ny, nx).copy()
+    dirs = [(1, 0), (-1, 0), (0, 1), (0, -1)] + ([(1, 1), (-1, -1), (1, -1), (-1, 1)] if conn == 10 else [])
+    for _ in range(int(frac * nx * ny * nz)):
+        k, j, i = rng.integers(nz), rng.integers(ny), rng.integers(nx)
+        di, dj = dirs[rng.integers(len(dirs))]
+        if 0 <= i + di < nx and 0 <= j + dj < ny:
+            p[k, j + dj, i + di] = p[k, j, i]
+    prob.p = p.reshape(-1)
+    return prob

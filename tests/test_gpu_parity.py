@@ -86,18 +86,53 @@ def test_parity_vs_oracle(shape, conn, precision, c_r):
         assert np.allclose(out["vals"][d].astype(np.float64), out["diag"], rtol=2 * C.EPS32, atol=0)
 
 
-@pytest.mark.parametrize("shape", [(70, 41, 11), (72, 41, 11)])  # per-lane and 16-byte-chunk input paths
+@pytest.mark.parametrize("shape", [(70, 41, 11), (72, 41, 11), (71, 41, 11)])
 @pytest.mark.parametrize("conn", [6, 10])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("c_r", [0.0, 1e-9])
 def test_kernel_variants_bit_identical(shape, conn, precision, c_r):
+    """Every variant gives the naive kernel's bits (TILED2 runs TILED where it
+    does not apply: odd nx, the FP64 path)."""
     prob = problem(shape, conn, precision, c_r=c_r, seed=3)
     a = run_gpu(prob, precision, "naive")
-    b = run_gpu(prob, precision, "tiled")
-    assert np.array_equal(a["R"].view(np.uint64), b["R"].view(np.uint64))
-    assert np.array_equal(a["vals"], b["vals"])
-    if precision == "mixed":
-        assert np.array_equal(a["diag"].view(np.uint64), b["diag"].view(np.uint64))
+    for kernel in ["tiled", "tiled2", "auto"]:
+        b = run_gpu(prob, precision, kernel)
+        assert np.array_equal(a["R"].view(np.uint64), b["R"].view(np.uint64)), kernel
+        assert np.array_equal(a["vals"], b["vals"]), kernel
+        if precision == "mixed":
+            assert np.array_equal(a["diag"].view(np.uint64), b["diag"].view(np.uint64)), kernel
+
+
+# nx even (the two-cell march's condition): one pair, one exact segment, a
+# segment plus a 2-cell tail, a segment plus a 30-cell tail, several
+# segments with ragged y-runs, single rows and more planes than a block holds.
+X2_SHAPES = [(2, 3, 2), (64, 5, 3), (66, 9, 5), (94, 7, 4), (128, 66, 9), (130, 41, 11), (256, 1, 6), (6, 70, 1)]
+
+
+@pytest.mark.parametrize("shape", X2_SHAPES)
+@pytest.mark.parametrize("conn", [6, 10])
+@pytest.mark.parametrize("c_r", [0.0, 1e-9])
+def test_two_cell_march_bit_identical(shape, conn, c_r):
+    """The march with two cells per lane (links as paired halves, x-links and
+    the links into the previous row reused by negation, ties recomputed
+    after the march) gives the naive kernel's bits under every tiling."""
+    prob = problem(shape, conn, "mixed", c_r=c_r, seed=5)
+    a = run_gpu(prob, "mixed", "naive")
+    for tiling in [(32, 4), (1, 8), (7, 4), (64, 8), (16, 4)]:
+        _same_bits(a, run_gpu(prob, "mixed", "tiled2", tiling=tiling), "mixed")
+
+
+@pytest.mark.parametrize("conn", [6, 10])
+@pytest.mark.parametrize("shape", [(130, 37, 5), (64, 64, 3)])
+def test_two_cell_march_ties_in_every_direction(conn, shape):
+    """Exact ties dPhi == 0 on x, y and diagonal links, inside a lane's pair,
+    across lanes and across segments: the reused links at a tie are
+    recomputed, so the rows equal the naive kernel's bit for bit."""
+    prob = C.tie_pairs_problem("mixed", conn, shape=shape)
+    a = run_gpu(prob, "mixed", "naive")
+    for tiling in [(32, 4), (5, 8)]:
+        _same_bits(a, run_gpu(prob, "mixed", "tiled2", tiling=tiling), "mixed")
+        _same_bits(a, run_gpu(prob, "mixed", "tiled", tiling=tiling), "mixed")
 
 
 def _same_bits(a, b, precision):
@@ -403,5 +438,5 @@ def test_reused_link_ties_are_fixed_up(precision, conn):
         vertical = (rows >= prob.nx) & (ref["col_idx"] < prob.nx)  # row-1 cells' links into row 0
         assert np.any(ref["dphi"][vertical] == 0.0)
     a = run_gpu(prob, precision, "naive")
-    for kernel in ["tiled", "tiled_tma"] if precision == "mixed" else ["tiled"]:
+    for kernel in ["tiled", "tiled_tma", "tiled2"] if precision == "mixed" else ["tiled"]:
         _same_bits(a, run_gpu(prob, precision, kernel), precision)
