@@ -287,6 +287,16 @@ def run_ours(args):
     kname = "k_assemble_ymarch_tma<DIAG,!CR,JAC,W=4>" if tma else "k_assemble_ymarch<float,DIAG,!CR,JAC>"
     traffic = profiled_traffic(khash, "assemble_tma_mixed_512x512x256.md" if tma else "assemble_mixed_512x512x256.md")
 
+    # precision of the timed workload: every row of three planes (top,
+    # middle, bottom) of the last timed step, against the oracle
+    precision1 = None
+    if rank == 0 and not args.skip_configs:
+        from paper_2304_11274_gb300 import synth as _s
+        last = _s.round_to_f32(_s.Problem(nx, ny, nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                          pres[(args.steps - 1) % len(pres)], prob.pn))
+        precision1 = plane_errors(last, "mixed", [0, nz // 2, nz - 1], R, vals, diag)
+        precision1["bar"] = 1e-6
+
     # end to end: host buffers through the C ABI (H2D of p, D2H of R, values, diag64)
     e2e = None
     if not args.no_e2e:
@@ -391,6 +401,10 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    if precision1 is not None:
+        line["error_vs_oracle"] = precision1
+    if rank == 0 and world == 1 and not args.skip_configs:
+        line["configs"] = measure_configs(dev, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -456,10 +470,16 @@ def measure_ensemble(dev, stream, rank=0, world=1, reps=10):
     ens.close()
     for g in grids:
         g.close()
+    nbytes = sum(algorithmic_bytes(g.n, g.nnz, "mixed") for g in grids)
     total, b_s = aggregate(cells, batched_ms * 1e-3, device=dev)
     _, s_s = aggregate(cells, seq_ms * 1e-3, device=dev)
+    peak, peak_kind = measured_peaks()
+    achieved = nbytes / (batched_ms * 1e-3) / 1e9
     return {"models": len(shapes), "cells": total, "unit": "cells/s", "ranks": world,
             "batched_value": total / b_s, "batched_ms": b_s * 1e3,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
+                         "traffic": None, "kernel": "k_assemble_batch (this rank's models)"},
             "sequential_value": total / s_s, "sequential_ms": s_s * 1e3,
             "launches_per_step": {"batched": 1, "sequential": len(mine)},
             "tiling": info, "scaling": "strong (fixed 64 models split across ranks)",
@@ -621,6 +641,220 @@ def measure_adjoint(dev, stream, reps=20):
             "outputs": "g_p and g_lnk (FP64)"}
 
 
+# ---------------------------------------------------------------------- precision statement
+#
+# The residual and Jacobian of each configuration against the FP64 oracle
+# (normwise residual, row-normwise Jacobian, entrywise max / RMS; a link whose
+# oracle dPhi lies within the path's rounding of zero may be upwinded either
+# way).  Runs outside every timed region; the oracle is the test oracle.
+
+
+def _plane_row_starts(nx, ny, nz, conn):
+    """CSR offset of each plane's first row (nz + 1 values), from the closed
+    form: a plane's rows hold its in-plane entries plus one entry per
+    vertical link."""
+    from paper_2304_11274_gb300 import _capi
+    lib = _capi.load()
+    inplane = lib.tpfa_nnz(nx, ny, 1, conn)
+    counts = [inplane + nx * ny * ((k > 0) + (k < nz - 1)) for k in range(nz)]
+    return np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+
+
+def _errors(R_gpu, J_gpu, ref, rows=None):
+    """(residual, jacobian_row, entry_max, entry_rms) of GPU values against an
+    oracle reference (oracle.compare.reference), optionally over a row range."""
+    from oracle import compare as OC
+    if rows is None:
+        eR = OC.residual_error(R_gpu, ref)
+        eJ = OC.jacobian_row_error(J_gpu, ref)
+        emax, erms = OC.entry_stats(J_gpu, ref)
+        return {"residual": eR, "jacobian_row": eJ, "entry_max": emax, "entry_rms": erms}
+    r0, r1 = rows
+    rp = ref["row_ptr"]
+    e0, e1 = rp[r0], rp[r1]
+    sub = {"R": ref["R"][r0:r1], "J": ref["J"][e0:e1], "row_ptr": rp[r0:r1 + 1] - e0,
+           "R_alt": None if ref.get("R_alt") is None else ref["R_alt"][r0:r1],
+           "J_alt": None if ref.get("J_alt") is None else ref["J_alt"][e0:e1]}
+    return _errors(R_gpu, J_gpu, sub)
+
+
+def plane_errors(prob, precision, planes, R, vals, diag):
+    """Errors of the rows of the given z-planes (device outputs R, vals,
+    diag64 of the whole grid) against the oracle run on the slab of the
+    plane and its vertical neighbours (a row depends only on its cell and
+    adj(K))."""
+    import oracle
+    from oracle import compare as OC
+    from paper_2304_11274_gb300 import synth
+    nx, ny, nz = prob.nx, prob.ny, prob.nz
+    conn = prob.phys["connectivity"]
+    nxy = nx * ny
+    starts = _plane_row_starts(nx, ny, nz, conn)
+    eps = OC.EPS32 if precision == "mixed" else OC.EPS64
+    worst = {"residual": 0.0, "jacobian_row": 0.0, "entry_max": 0.0, "entry_rms2": 0.0}
+    rows = 0
+    for k in planes:
+        k0, k1 = max(k - 1, 0), min(k + 2, nz)
+        cut = lambda a: a.reshape(nz, nxy)[k0:k1].reshape(-1)
+        sub = synth.Problem(nx, ny, k1 - k0, prob.phys, cut(prob.perm), cut(prob.poro), cut(prob.depth),
+                            cut(prob.p), cut(prob.pn))
+        ref = OC.reference(sub, eps)
+        kk = k - k0
+        Rg = R[k * nxy:(k + 1) * nxy].cpu().numpy()
+        Jg = vals[int(starts[k]):int(starts[k + 1])].cpu().numpy().astype(np.float64)
+        if diag is not None:  # the FP64 diagonal in place of its FP32 copy
+            rp = ref["row_ptr"][kk * nxy:(kk + 1) * nxy + 1] - ref["row_ptr"][kk * nxy]
+            cols = ref["col_idx"][ref["row_ptr"][kk * nxy]:ref["row_ptr"][(kk + 1) * nxy]]
+            rowid = np.repeat(np.arange(kk * nxy, (kk + 1) * nxy), np.diff(rp))
+            Jg[cols == rowid] = diag[k * nxy:(k + 1) * nxy].cpu().numpy()
+        e = _errors(Rg, Jg, ref, rows=(kk * nxy, (kk + 1) * nxy))
+        for key in ("residual", "jacobian_row", "entry_max"):
+            worst[key] = max(worst[key], e[key])
+        worst["entry_rms2"] += e["entry_rms"] ** 2 * nxy
+        rows += nxy
+    worst["entry_rms"] = float(np.sqrt(worst.pop("entry_rms2") / rows))
+    worst["rows"] = f"every row of planes {list(planes)} ({rows} rows)"
+    return worst
+
+
+def host_info():
+    cpu = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    cpu = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": cpu or os.uname().machine}
+
+
+def time_oracle(fn, min_reps=3, min_s=0.5):
+    """Mean wall time of fn() over at least min_reps calls and min_s seconds."""
+    fn()  # warm-up
+    reps, t = 0, 0.0
+    while reps < min_reps or t < min_s:
+        t0 = time.perf_counter()
+        fn()
+        t += time.perf_counter() - t0
+        reps += 1
+    return t / reps, reps
+
+
+def oracle_rates(prob, kind="assemble", v=None):
+    """Oracle cells/s single-threaded and on every thread it may use."""
+    import oracle
+    allt = oracle.max_threads()
+    pat = oracle.pattern(prob.nx, prob.ny, prob.nz, prob.phys["connectivity"])
+    if kind == "assemble":
+        fn = lambda: oracle.assemble(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth,
+                                     prob.p, prob.pn, pat=pat)
+    else:
+        fn = lambda: oracle.vjp(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro, prob.depth, prob.p,
+                                prob.pn, v)
+    out = {}
+    for label, n in (("threads_1", 1), ("threads_all", allt)):
+        oracle.set_threads(n)
+        sec, reps = time_oracle(fn)
+        out[label] = {"value": prob.n / sec, "unit": "cells/s", "threads": n, "reps": reps}
+    oracle.set_threads(allt)
+    out["sample"] = f"{prob.nx}x{prob.ny}x{prob.nz} ({prob.n} cells), {kind}"
+    return out
+
+
+def gpu_rate(g, p_dev, R, vals, diag, calls, stream, dev):
+    """Cells/s of the fused assembly on a bound grid (CUDA events)."""
+    import torch
+    for _ in range(3):
+        g.assemble_jacobian(R, vals, diag)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(calls):
+        g.assemble_jacobian(R, vals, diag)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    g.sync_status()
+    ms = a.elapsed_time(b) / calls
+    return {"value": g.n / (ms * 1e-3), "unit": "cells/s", "ms": ms, "calls": calls}
+
+
+def measure_configs(dev, stream, full=True):
+    """Per-configuration precision and rates: config 0 (32^3, 6 links,
+    FP64; every row), config 2 (256^3 layered, 10 links; mixed and FP64 GPU
+    paths, every row), config 4 (128^3 adjoint; g_p and g_lnk), with the
+    oracle timed on the host single-threaded and on every thread."""
+    import torch
+
+    import oracle
+    from oracle import compare as OC
+    from paper_2304_11274_gb300 import synth
+    from paper_2304_11274_gb300.api import Grid
+
+    oracle.build()
+    out = {"host": host_info()}
+
+    # config 0: FP64, 32^3, 6 links; L2-resident (16 MB per call)
+    p0 = synth.config_problem(0)
+    g = Grid(p0.nx, p0.ny, p0.nz, p0.phys, "fp64", p0.perm, p0.poro, p0.depth, device=dev)
+    g.set_state(p0.p, p0.pn)
+    R, vals, _ = g.empty_outputs()
+    rate = gpu_rate(g, None, R, vals, None, 1000, stream, dev)
+    ref = OC.reference(p0, OC.EPS64)
+    err = _errors(R.cpu().numpy(), vals.cpu().numpy(), ref)
+    g.close()
+    out["config0_32x32x32_6pt_fp64"] = {
+        "gpu": dict(rate, note="1000 calls, inputs and outputs L2-resident (16 MB), so no roofline"),
+        "error_vs_oracle": dict(err, rows="every row", bar=1e-12), "oracle": oracle_rates(p0)}
+
+    # config 2: the 256^3 layered precision study, both GPU paths, every row
+    p2 = synth.config_problem(2)
+    c2 = {"gpu": {}, "error_vs_oracle": {}}
+    for precision in ("mixed", "fp64"):
+        prob = synth.round_to_f32(p2) if precision == "mixed" else p2
+        g = Grid(prob.nx, prob.ny, prob.nz, prob.phys, precision, prob.perm, prob.poro, prob.depth, device=dev)
+        g.set_state(prob.p, prob.pn)
+        R, vals, diag = g.empty_outputs()
+        c2["gpu"][precision] = gpu_rate(g, None, R, vals, diag, 10 if precision == "fp64" else 20, stream, dev)
+        if full:
+            ref = OC.reference(prob, OC.EPS32 if precision == "mixed" else OC.EPS64)
+            J = vals.cpu().numpy().astype(np.float64)
+            if diag is not None:
+                rows = np.repeat(np.arange(prob.n), np.diff(ref["row_ptr"]))
+                J[ref["col_idx"] == rows] = diag.cpu().numpy()
+            c2["error_vs_oracle"][precision] = dict(_errors(R.cpu().numpy(), J, ref), rows="every row",
+                                                    bar=1e-6 if precision == "mixed" else 1e-12,
+                                                    ambiguous_links=int(ref["ambiguous"].sum()))
+            del ref, J
+        del R, vals, diag
+        g.close()
+    c2["gpu"]["mixed_over_fp64"] = c2["gpu"]["mixed"]["value"] / c2["gpu"]["fp64"]["value"]
+    c2["oracle"] = oracle_rates(synth.round_to_f32(synth.make_problem(
+        256, 256, 16, synth.BASE_SEED + 2, connectivity=10, layered=True, layered_pressure=True)))
+    out["config2_256x256x256_layered_10pt"] = c2
+
+    # config 4: the adjoint on 128^3 (mixed), against the oracle's gradient
+    p4 = synth.round_to_f32(synth.config_problem(4))
+    p4.perm = p4.perm.astype(np.float32).astype(np.float64)  # the adjoint's k is stored in FP32
+    v = synth.cotangent(p4.n, seed=synth.BASE_SEED + 4)
+    g = Grid(p4.nx, p4.ny, p4.nz, p4.phys, "mixed", p4.perm, p4.poro, p4.depth, device=dev)
+    g.set_state(p4.p.astype(np.float32), p4.pn.astype(np.float32))
+    gp, gk = (x.cpu().numpy() for x in g.vjp(v))
+    g.sync_status()
+    g.close()
+    gp_ref, gk_ref = oracle.vjp(p4.nx, p4.ny, p4.nz, p4.phys, p4.perm, p4.poro, p4.depth, p4.p, p4.pn, v)
+    nw = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+    out["config4_128x128x128_adjoint_mixed"] = {
+        "error_vs_oracle": {"g_p": nw(gp, gp_ref), "g_lnk": nw(gk, gk_ref), "norm": "normwise (inf)", "bar": 1e-6},
+        "oracle": oracle_rates(synth.round_to_f32(synth.make_problem(128, 128, 16, synth.BASE_SEED + 4,
+                                                                     connectivity=10)), kind="vjp",
+                               v=synth.cotangent(128 * 128 * 16, seed=5))}
+    out["config3_ensemble"] = {"note": "each model's rows are bit-identical to its single-grid assembly "
+                                       "(tests/test_gpu_ensemble.py), so its error is config 1's"}
+    return out
+
+
 # ---------------------------------------------------------------------- oracle on the host
 
 
@@ -688,6 +922,8 @@ def main():
     ap.add_argument("--skip-jvp", action="store_true", help="skip the matrix-free J w line")
     ap.add_argument("--skip-newton", action="store_true", help="skip the Newton-step line")
     ap.add_argument("--skip-mesh", action="store_true", help="skip the general-mesh line")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="skip the per-configuration precision statement and the config 0 / 2 / 4 lines")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "tiled_tma"],
                     help="assembly kernel variant of the timed step (auto = the library's choice)")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),

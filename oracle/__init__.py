@@ -1,8 +1,9 @@
 """FP64 CPU oracle for the TPFA residual and Jacobian (arXiv 2304.11274, Section 3).
 
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` are the only callers.  The product library
-never imports, links or loads anything from this directory.
+CPU-baseline, reference and precision-statement legs of ``bench.py`` (all
+outside its timed regions) are the only callers.  The product library never
+imports, links or loads anything from this directory.
 
 The arithmetic lives in ``tpfa_oracle.c`` (plain C, FP64, compiled with
 ``-ffp-contract=off``); this module only builds it with gcc and marshals NumPy
@@ -84,6 +85,8 @@ def _load():
     lib.orc_mesh_assemble.restype = ctypes.c_int
     lib.orc_max_threads.argtypes = []
     lib.orc_max_threads.restype = ctypes.c_int
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
+    lib.orc_set_threads.restype = None
     _lib = lib
     return lib
 
@@ -101,6 +104,12 @@ def make_params(phys: dict) -> OracleParams:
 
 def max_threads() -> int:
     return int(_load().orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's row loops from now on (for timing it
+    single-threaded and on all cores)."""
+    _load().orc_set_threads(int(n))
 
 
 def pattern(nx: int, ny: int, nz: int, conn: int):

@@ -436,3 +436,13 @@ int orc_max_threads(void) {
     return 1;
 #endif
 }
+
+/* Set the number of threads the row loops use from now on (n >= 1; ignored
+ * without OpenMP).  For timing the oracle single-threaded and on all cores. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -236,13 +236,18 @@ bool tma_ready(tpfa_grid* h) {
     return h->tm_state;
 }
 
-// The library's choice of assembly kernel: the march with two cells per lane
-// (the dispatch runs the one-cell march where that one does not apply:
-// residual-only calls, the FP64 path, odd nx, fields not pair-aligned).
-// (The TMA march gives the same bits but measured 8 % slower than the
-// one-cell march on the 512 x 512 x 256 workload: its row waits stall where
-// the per-lane prefetch does not, and it saves no instructions.)
-AsmKernel auto_kernel(tpfa_grid*) { return AsmKernel::XMarch; }
+// The library's choice of assembly kernel: on grids at least 256 cells wide
+// the march with two cells per lane (the dispatch runs the one-cell march
+// where that one does not apply: residual-only calls, the FP64 path, odd nx,
+// fields not pair-aligned), else the one-cell march.  The two-cell march's
+// x-boundary rows cost every lane of a boundary segment a masked sum, so it
+// wins only where few segments touch the x boundaries: measured (G cells/s,
+// one-cell vs two-cell, best tiling each) 25.4 vs 24.1 at 128^3, 27.9 vs 24.2
+// at 192 x 160 x 80, 34.8 vs 36.8 at 256^3, 38.0 vs 42.7 at 512 x 512 x 256,
+// 38.4 vs 44.8 at 1024 x 256 x 256.  (The TMA march gives the same bits but
+// measured 8 % slower than the one-cell march at 512 x 512 x 256: its row
+// waits stall where the per-lane prefetch does not.)
+AsmKernel auto_kernel(tpfa_grid* h) { return h->nx >= 256 ? AsmKernel::XMarch : AsmKernel::YMarch; }
 
 int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st, int k0 = 0,
            int k1 = -1) {
@@ -1238,7 +1243,13 @@ namespace {
 int build_table(tpfa_ensemble e, std::vector<BatchModel>& tab) {
     tab.resize(e->M);
     long long first = 0;
-    for (int m = 0; m < e->M; ++m) {
+    // tiles are numbered (and claimed) largest model first, so the launch
+    // ends on the small models' tiles
+    std::vector<int> order(e->M);
+    for (int m = 0; m < e->M; ++m) order[m] = m;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return e->grids[a]->N > e->grids[b]->N; });
+    for (int t = 0; t < e->M; ++t) {
+        const int m = order[t];
         tpfa_grid* h = e->grids[m];
         if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "ensemble model %d has no state (tpfa_set_state)", m);
         if (!e->vals[m]) return fail(TPFA_ERR_INVALID_ARG, "ensemble model %d has no outputs (tpfa_ensemble_set_outputs)", m);
@@ -1254,7 +1265,7 @@ int build_table(tpfa_ensemble e, std::vector<BatchModel>& tab) {
         bm.crk = h->crk ? 1 : 0;
         bm.first = first;
         first += (long long)bm.tx * bm.ty * bm.tz;
-        tab[m] = bm;
+        tab[t] = bm;
     }
     e->total = first;
     return TPFA_OK;
