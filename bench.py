@@ -1,4 +1,4 @@
-"""Benchmark: cells/s of the TPFA residual + Jacobian assembly on one GB300.
+"""Benchmark: cells/s of the TPFA residual + Jacobian assembly on GB300s.
 
 Workload (default): the paper-shaped grid, 512 x 512 x 256 cells (67.1 M),
 10 links per cell (4 cardinal + 4 diagonal in-plane, 2 vertical), mixed
@@ -10,8 +10,10 @@ with a new pressure vector (the repeated-application protocol of Section 3:
 are cycled.  Inputs and outputs (~6.7 GB per step) exceed the 129 MB L2, so
 no flush is needed between steps.
 
-Multi-GPU (torchrun): every rank assembles its own replica grid (no
-collective on the data path); value = all ranks' cells / max-over-ranks time.
+Multi-GPU (torchrun, N > 1): the grid is split into N z-slabs, one per rank;
+every step exchanges one plane of pressure with each neighbouring slab (NCCL
+point-to-point) and assembles the owned rows; value = the grid's cells /
+max-over-ranks time (strong scaling).
 
 --impl reference times the FP64 CPU oracle (the test oracle, unmodified) on
 the host cores on a bounded sample of the same workload.
@@ -196,13 +198,125 @@ def algorithmic_bytes(n, nnz, precision, crk=False):
 # ---------------------------------------------------------------------- our arm
 
 
+def run_sharded(args, rank, world, local):
+    """N > 1 GPUs: the one grid split into z-slabs, one per rank (strong
+    scaling: the total work is the 512 x 512 x 256 assembly whatever N).
+    One step = the halo exchange (each rank sends its first and last owned
+    planes of pressure to its neighbours and receives theirs, NCCL
+    point-to-point) + the assembly of the owned rows; value = the grid's
+    cells x steps / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2304_11274_gb300 import build as libbuild
+    from paper_2304_11274_gb300 import synth
+    from paper_2304_11274_gb300.api import Slab, slab_bounds
+    from paper_2304_11274_gb300.distributed import slab_halo_exchange
+
+    dev = torch.device("cuda", local)
+    libbuild.build()
+    nx, ny, nz = args.shape
+    nxy = nx * ny
+    k0, k1, e0, e1 = slab_bounds(nz, world, rank)
+    prob = synth.make_problem(nx, ny, nz, synth.BASE_SEED + 1, connectivity=CONN)
+    pres = [prob.p] + synth.pressure_sequence(prob, 7, seed=synth.BASE_SEED + 11)
+    cut = lambda a: np.ascontiguousarray(a[e0 * nxy:e1 * nxy])
+    g = Slab(nx, ny, nz, k0, k1, prob.phys, "mixed", cut(prob.perm), cut(prob.poro), cut(prob.depth), device=dev)
+    p_dev = [torch.as_tensor(cut(x).astype(np.float32), device=dev) for x in pres]
+    g.set_state(p_dev[0], torch.as_tensor(cut(prob.pn).astype(np.float32), device=dev))
+    tiling = g.autotune(None)
+    R, vals, diag = g.empty_outputs()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s):
+        p = p_dev[s % len(p_dev)]
+        slab_halo_exchange(p, nxy, k0, k1, e0, e1, rank, world)
+        g.set_pressure(p)
+        g.assemble_jacobian(R, vals, diag)
+
+    for s in range(args.warmup):
+        step(s)
+    g.sync_status()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(args.steps):
+        step(s)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clk = clocks.stop()
+    g.sync_status()
+    ms = torch.tensor([t0.elapsed_time(t1)], device=dev)
+    dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    total_ms = float(ms.item())
+    value = prob.n * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public API: pinned host pressure of the slab up,
+    # halo exchange, assembly, the owned rows' R, values and diag64 down
+    Ro, vo, do = g.owned(R, vals, diag)
+    ph = [torch.as_tensor(cut(x).astype(np.float32)).pin_memory() for x in pres[:2]]
+    Rh, vh, dh = (torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in (Ro, vo, do))
+    e2e_steps = max(3, min(args.steps, 10))
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter()
+    for s in range(e2e_steps):
+        p = p_dev[0]
+        p.copy_(ph[s % 2], non_blocking=True)
+        slab_halo_exchange(p, nxy, k0, k1, e0, e1, rank, world)
+        g.set_pressure(p)
+        g.assemble_jacobian(R, vals, diag)
+        Rh.copy_(Ro, non_blocking=True)
+        vh.copy_(vo, non_blocking=True)
+        dh.copy_(do, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    es = torch.tensor([time.perf_counter() - te], device=dev)
+    dist.all_reduce(es, op=dist.ReduceOp.MAX)
+    e2e = {"value": prob.n * e2e_steps / float(es.item()), "unit": "cells/s",
+           "h2d_bytes_per_step": prob.n * 4, "d2h_bytes_per_step": prob.n * 16 + 4 * g.lib.tpfa_nnz(nx, ny, nz, CONN),
+           "steps": e2e_steps, "api": "Slab.assemble_jacobian with pinned host copies, all ranks"}
+    nbytes = algorithmic_bytes(prob.n, g.lib.tpfa_nnz(nx, ny, nz, CONN), "mixed")
+    peak, peak_kind = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; log10 k ~ N(-13, 0.5), phi0 ~ U[0.1, 0.3], hydrostatic + U[-1e5, 1e5] Pa)",
+        "config": {"workload": WORKLOAD if tuple(args.shape) == SHAPE else
+                   "tpfa_residual_jacobian_%dx%dx%d_10pt_mixed" % tuple(args.shape), "grid": list(args.shape),
+                   "cells": prob.n, "links_per_cell": CONN,
+                   "parallelism": f"z-slabs x{world} (one plane of pressure exchanged each way per step, NCCL)",
+                   "l2": "inputs+outputs 6.7 GB per step > 129 MB L2; no flush",
+                   "tiling_rank0": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]}},
+        "roofline": {"bound": "hbm", "achieved": nbytes / (total_ms * 1e-3 / args.steps) / 1e9 / world,
+                     "peak": peak, "unit": "GB/s per GPU", "peak_kind": peak_kind,
+                     "frac": nbytes / (total_ms * 1e-3 / args.steps) / 1e9 / world / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": nbytes / world,
+                     "note": "whole-step time (exchange included) against each GPU's share of the bytes"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": args.steps,
+        "ensemble": None if args.skip_ensemble else measure_ensemble(dev, stream, rank, world),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    dist.destroy_process_group()
+
+
 def run_ours(args):
     import torch
 
     rank, world, local = env_rank()
-    if world > 1:
+    if world > 1 or args.slabs:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return run_sharded(args, rank, world, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -922,6 +1036,8 @@ def main():
     ap.add_argument("--skip-jvp", action="store_true", help="skip the matrix-free J w line")
     ap.add_argument("--skip-newton", action="store_true", help="skip the Newton-step line")
     ap.add_argument("--skip-mesh", action="store_true", help="skip the general-mesh line")
+    ap.add_argument("--slabs", action="store_true",
+                    help="run the z-slab decomposition even on one rank (under torchrun; N > 1 always does)")
     ap.add_argument("--skip-configs", action="store_true",
                     help="skip the per-configuration precision statement and the config 0 / 2 / 4 lines")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "tiled_tma"],

@@ -269,6 +269,61 @@ int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* str
  */
 int tpfa_sync_status(tpfa_handle h, void* stream);
 
+/* ---------------------------------------------------------------- z-slabs of one grid */
+
+/*
+ * Decomposition of one grid over several GPUs into z-slabs.  Section 5 maps
+ * the x-y plane of cells onto a grid of processing elements, keeps each
+ * column's z-range in the element's memory and exchanges the neighbouring
+ * values across element boundaries (Section 5.2); here each GPU holds a
+ * contiguous range of z-planes and exchanges one plane of pressure with each
+ * neighbouring slab before an assembly.  In-plane (cardinal and diagonal)
+ * links never cross a slab boundary, so no corner cells are exchanged.
+ *
+ * tpfa_slab_bounds (host-only, needs no GPU): the planes [k0, k1) of slab
+ * `part` of `parts` over nz planes (balanced: the first nz % parts slabs
+ * hold one plane more; 1 <= parts <= nz) and the planes [e0, e1) its handle
+ * holds: the slab and one halo plane on each side that exists.
+ */
+int tpfa_slab_bounds(int nz, int parts, int part, int* k0, int* k1, int* e0, int* e1);
+
+/*
+ * A slab handle: planes [k0, k1) of an nx x ny x nz grid.  perm_dev,
+ * poro_dev and depth_dev hold the planes [e0, e1) of tpfa_slab_bounds (N =
+ * nx ny (e1 - e0) doubles each; read during the call), so the handle's
+ * owned transmissibilities include the vertical links into its halos.  The
+ * handle behaves as a grid of e1 - e0 planes (tpfa_set_state /
+ * tpfa_set_pressure bind N values, halo planes included, and every output
+ * has the sizes of that grid: N residuals, its nnz values, N diagonals),
+ * but tpfa_assemble_jacobian and tpfa_assemble_residual write only the rows
+ * of the owned planes (tpfa_slab_info gives their ranges); those rows equal
+ * the larger grid's rows bit for bit once the halo planes of the bound
+ * pressure hold the neighbouring slabs' values (tpfa_slab_exchange, or any
+ * copy such as an NCCL send/receive).  The kernel variant is the library's
+ * choice (a naive request runs the tiled march).  tpfa_vjp, tpfa_jvp, the
+ * Krylov / Newton calls, the host-buffer call and ensembles return
+ * TPFA_ERR_INVALID_ARG on slabs.
+ */
+int tpfa_create_slab(tpfa_handle* out, int nx, int ny, int nz, int k0, int k1, const tpfa_params* prm,
+                     tpfa_precision prec, const double* perm_dev, const double* poro_dev, const double* depth_dev,
+                     void* stream);
+
+/* A slab's owned planes: [k0, k1) of the larger grid and [own0, own1) of the
+ * handle; its owned rows are cells [row0, row1) and CSR entries
+ * [entry0, entry1) of the handle's outputs.  Any out-pointer may be NULL. */
+int tpfa_slab_info(tpfa_handle h, int* k0, int* k1, int* own0, int* own1, long long* row0, long long* row1,
+                   long long* entry0, long long* entry1);
+
+/*
+ * Halo exchange between adjacent slabs (upper's k0 == lower's k1) of one
+ * grid, possibly on different devices: copies lower's last owned plane of
+ * pressure into upper's bottom halo plane and upper's first owned plane into
+ * lower's top halo plane (cudaMemcpyPeerAsync, asynchronous on `stream`).
+ * p_lower_dev / p_upper_dev: the pressures bound (or to be bound) to each
+ * slab, N values of the field type each.
+ */
+int tpfa_slab_exchange(tpfa_handle lower, void* p_lower_dev, tpfa_handle upper, void* p_upper_dev, void* stream);
+
 /* ---------------------------------------------------------------- tiling */
 
 /*

@@ -91,6 +91,11 @@ SIGNATURES = [
     ("tpfa_grid_info", _I, [_VP] + [ctypes.POINTER(_I)] * 4 + [ctypes.POINTER(_LL), ctypes.POINTER(_I)]),
     ("tpfa_get_transmissibility", _I, [_VP, _I, _VP, _VP]),
     ("tpfa_sync_status", _I, [_VP, _VP]),
+    ("tpfa_slab_bounds", _I, [_I, _I, _I] + [ctypes.POINTER(_I)] * 4),
+    ("tpfa_create_slab", _I, [ctypes.POINTER(_VP), _I, _I, _I, _I, _I, ctypes.POINTER(TPFAParams), _I, _VP, _VP, _VP,
+                              _VP]),
+    ("tpfa_slab_info", _I, [_VP] + [ctypes.POINTER(_I)] * 4 + [ctypes.POINTER(_LL)] * 4),
+    ("tpfa_slab_exchange", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_set_tiling", _I, [_VP, _I, _I]),
     ("tpfa_get_tiling", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("tpfa_autotune", _I, [_VP, ctypes.c_char_p, _VP]),

@@ -70,14 +70,17 @@ class Grid:
             ph = _dev_f64(poro, self.device)
             z = _dev_f64(depth, self.device)
             h = ctypes.c_void_p()
-            check(self.lib.tpfa_create_grid(ctypes.byref(h), self.nx, self.ny, self.nz, ctypes.byref(prm),
-                                            PRECISIONS[precision], _ptr(k), _ptr(ph), _ptr(z), _stream()))
+            self._create(h, prm, k, ph, z)
         self.handle = h
         nnz = ctypes.c_longlong()
         check(self.lib.tpfa_grid_info(h, None, None, None, None, ctypes.byref(nnz), None))
         self.nnz = int(nnz.value)
         self._p = None
         self._pn = None
+
+    def _create(self, h, prm, k, ph, z):
+        check(self.lib.tpfa_create_grid(ctypes.byref(h), self.nx, self.ny, self.nz, ctypes.byref(prm),
+                                        PRECISIONS[self.precision], _ptr(k), _ptr(ph), _ptr(z), _stream()))
 
     # -- lifetime
     def close(self):
@@ -264,6 +267,57 @@ class Grid:
         path = cache_path.encode() if cache_path else None
         check(self.lib.tpfa_autotune(self.handle, path, _stream(stream)))
         return self.tiling()
+
+
+def slab_bounds(nz, parts, part):
+    """(k0, k1, e0, e1): the planes [k0, k1) of z-slab `part` of `parts` and
+    the planes [e0, e1) its handle holds (the slab and its halo planes)."""
+    lib = _capi.load()
+    v = [ctypes.c_int() for _ in range(4)]
+    check(lib.tpfa_slab_bounds(int(nz), int(parts), int(part), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+class Slab(Grid):
+    """Planes [k0, k1) of an nx x ny x nz grid with one halo plane on each
+    side that exists (a z-slab of a decomposition over GPUs; Section 5's
+    element-per-column mapping with the exchange of neighbour values).
+
+    perm, poro, depth, and the pressures bound later, hold the planes [e0, e1)
+    of slab_bounds: n = nx ny (e1 - e0) values.  Outputs have the sizes of
+    that local grid; assemblies write only the owned rows (see owned()),
+    which equal the whole grid's rows once the halo planes hold the
+    neighbouring slabs' pressure (exchange_with, or
+    distributed.slab_halo_exchange across processes)."""
+
+    def __init__(self, nx, ny, nz, k0, k1, phys, precision, perm, poro, depth, device="cuda"):
+        self.nz_global, self.k0, self.k1 = int(nz), int(k0), int(k1)
+        e0, e1 = max(self.k0 - 1, 0), min(self.k1 + 1, self.nz_global)
+        self.e0, self.e1 = e0, e1
+        super().__init__(nx, ny, e1 - e0, phys, precision, perm, poro, depth, device)
+        k0_, k1_, o0, o1 = (ctypes.c_int() for _ in range(4))
+        r0, r1, n0, n1 = (ctypes.c_longlong() for _ in range(4))
+        check(self.lib.tpfa_slab_info(self.handle, *[ctypes.byref(x) for x in (k0_, k1_, o0, o1, r0, r1, n0, n1)]))
+        self.own = (o0.value, o1.value)
+        self.rows = (r0.value, r1.value)
+        self.entries = (n0.value, n1.value)
+
+    def _create(self, h, prm, k, ph, z):
+        check(self.lib.tpfa_create_slab(ctypes.byref(h), self.nx, self.ny, self.nz_global, self.k0, self.k1,
+                                        ctypes.byref(prm), PRECISIONS[self.precision], _ptr(k), _ptr(ph), _ptr(z),
+                                        _stream()))
+
+    def owned(self, R=None, vals=None, diag=None):
+        """Views of the owned rows of this slab's outputs."""
+        r0, r1 = self.rows
+        e0, e1 = self.entries
+        return (None if R is None else R[r0:r1], None if vals is None else vals[e0:e1],
+                None if diag is None else diag[r0:r1])
+
+    def exchange_with(self, upper, p_self, p_upper, stream=None):
+        """Copy the halo planes between this slab (the lower one) and the
+        adjacent `upper` slab (peer copies; same or different devices)."""
+        check(self.lib.tpfa_slab_exchange(self.handle, _ptr(p_self), upper.handle, _ptr(p_upper), _stream(stream)))
 
 
 class Ensemble:
@@ -467,4 +521,4 @@ def residual(grid, p, log_k):
     return TPFAResidual.apply(grid, p, log_k)
 
 
-__all__ = ["Grid", "Ensemble", "TPFAError", "PRECISIONS", "TPFAResidual", "residual"]
+__all__ = ["Grid", "Slab", "slab_bounds", "Ensemble", "TPFAError", "PRECISIONS", "TPFAResidual", "residual"]

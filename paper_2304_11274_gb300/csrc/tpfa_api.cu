@@ -120,6 +120,13 @@ struct tpfa_grid {
     int JY = 32;  // rows per warp march (tpfa_autotune may change it)
     int sms = 0;  // multiprocessors of the grid's device
     int W = 4;    // warps (z-planes) per block
+    // a z-slab of a larger grid (tpfa_create_slab): the handle's planes are
+    // the slab and its one-plane halos; assemblies write the rows of the
+    // owned planes [own0, own1) only
+    bool slab = false;
+    int own0 = 0, own1 = 0;       // owned planes, local numbering
+    int slab_k0 = 0, slab_k1 = 0; // owned planes, the larger grid's numbering
+    int slab_nz = 0;              // planes of the larger grid
     // tensor maps of the TMA march (mixed path): the library-owned fields'
     // maps are encoded once (tm_static: 0 not yet, 1 done, -1 impossible),
     // those of p and p^n whenever the bound pointers change
@@ -252,6 +259,11 @@ AsmKernel auto_kernel(tpfa_grid* h) { return h->nx >= 256 ? AsmKernel::XMarch : 
 int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st, int k0 = 0,
            int k1 = -1) {
     cudaError_t e;
+    if (h->slab) {  // a slab assembles its owned planes only
+        if (kern == AsmKernel::Naive) kern = AsmKernel::YMarch;
+        k0 = h->own0;
+        k1 = h->own1;
+    }
     if (kern == AsmKernel::YMarchTma && !tma_ready(h))
         return fail(TPFA_ERR_INVALID_ARG,
                     "the TMA march needs the mixed path, nx a multiple of 4 and 16-byte aligned p and p^n");
@@ -647,6 +659,7 @@ int tpfa_assemble_jacobian_host(tpfa_handle h, const void* p_host, double* R_hos
     if (rc) return rc;
     if (!p_host) return fail(TPFA_ERR_INVALID_ARG, "p_host must be non-NULL");
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    if (h->slab) return fail(TPFA_ERR_INVALID_ARG, "this call is not available on a slab handle (assembly only)");
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t pb = h->real_size * (size_t)h->N;
@@ -764,6 +777,7 @@ int tpfa_vjp_kernel(tpfa_handle h, tpfa_kernel kern, const double* v_dev, double
     if (rc) return rc;
     if (!v_dev || !g_p_dev) return fail(TPFA_ERR_INVALID_ARG, "v and g_p must be non-NULL");
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    if (h->slab) return fail(TPFA_ERR_INVALID_ARG, "this call is not available on a slab handle (assembly only)");
     AsmKernel k;
     switch (kern) {
         case TPFA_KERNEL_AUTO:
@@ -794,6 +808,7 @@ int tpfa_jvp_kernel(tpfa_handle h, tpfa_kernel kern, const double* w_dev, double
     if (rc) return rc;
     if (!w_dev || !Jw_dev) return fail(TPFA_ERR_INVALID_ARG, "w and Jw must be non-NULL");
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    if (h->slab) return fail(TPFA_ERR_INVALID_ARG, "this call is not available on a slab handle (assembly only)");
     AsmKernel k;
     switch (kern) {
         case TPFA_KERNEL_AUTO:
@@ -823,6 +838,7 @@ int tpfa_linear_solve(tpfa_handle h, const double* b_dev, double* x_dev, const t
     if (rc) return rc;
     if (!b_dev || !x_dev) return fail(TPFA_ERR_INVALID_ARG, "b and x must be non-NULL");
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    if (h->slab) return fail(TPFA_ERR_INVALID_ARG, "this call is not available on a slab handle (assembly only)");
     DeviceGuard dg(h->device);
     rc = krylov_workspace(h);
     if (rc) return rc;
@@ -838,6 +854,7 @@ int tpfa_newton_step(tpfa_handle h, void* p_dev, const tpfa_krylov_opts* opts, t
     if (rc) return rc;
     if (!p_dev) return fail(TPFA_ERR_INVALID_ARG, "p must be non-NULL");
     if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    if (h->slab) return fail(TPFA_ERR_INVALID_ARG, "this call is not available on a slab handle (assembly only)");
     DeviceGuard dg(h->device);
     rc = krylov_workspace(h);
     if (rc) return rc;
@@ -928,6 +945,85 @@ int tpfa_get_transmissibility(tpfa_handle h, int which, void* out_dev, void* str
     cudaError_t e = cudaMemcpyAsync(out_dev, h->T[which], h->real_size * (size_t)h->N, cudaMemcpyDeviceToDevice,
                                     static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "transmissibility copy");
+    return TPFA_OK;
+}
+
+int tpfa_slab_bounds(int nz, int parts, int part, int* k0, int* k1, int* e0, int* e1) {
+    if (nz < 1 || parts < 1 || part < 0 || part >= parts || parts > nz)
+        return fail(TPFA_ERR_INVALID_ARG, "slab bounds: need 1 <= parts <= nz and 0 <= part < parts (nz %d, parts %d, "
+                    "part %d)", nz, parts, part);
+    // balanced: the first nz % parts slabs hold one plane more
+    const int base = nz / parts, extra = nz % parts;
+    const int a = part * base + (part < extra ? part : extra);
+    const int b = a + base + (part < extra ? 1 : 0);
+    if (k0) *k0 = a;
+    if (k1) *k1 = b;
+    if (e0) *e0 = a > 0 ? a - 1 : 0;
+    if (e1) *e1 = b < nz ? b + 1 : nz;
+    return TPFA_OK;
+}
+
+int tpfa_create_slab(tpfa_handle* out, int nx, int ny, int nz, int k0, int k1, const tpfa_params* prm,
+                     tpfa_precision prec, const double* perm_dev, const double* poro_dev, const double* depth_dev,
+                     void* stream) {
+    g_err.clear();
+    if (!out) return fail(TPFA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nz < 1 || k0 < 0 || k1 > nz || k0 >= k1)
+        return fail(TPFA_ERR_INVALID_ARG, "slab planes [%d, %d) are not a non-empty range of [0, %d)", k0, k1, nz);
+    const int e0 = k0 > 0 ? k0 - 1 : 0, e1 = k1 < nz ? k1 + 1 : nz;
+    tpfa_handle h = nullptr;
+    int rc = tpfa_create_grid(&h, nx, ny, e1 - e0, prm, prec, perm_dev, poro_dev, depth_dev, stream);
+    if (rc) return rc;
+    h->slab = true;
+    h->own0 = k0 - e0;
+    h->own1 = k1 - e0;
+    h->slab_k0 = k0;
+    h->slab_k1 = k1;
+    h->slab_nz = nz;
+    *out = h;
+    return TPFA_OK;
+}
+
+int tpfa_slab_info(tpfa_handle h, int* k0, int* k1, int* own0, int* own1, long long* row0, long long* row1,
+                   long long* entry0, long long* entry1) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->slab) return fail(TPFA_ERR_INVALID_ARG, "not a slab handle");
+    const long long nxy = (long long)h->nx * h->ny;
+    if (k0) *k0 = h->slab_k0;
+    if (k1) *k1 = h->slab_k1;
+    if (own0) *own0 = h->own0;
+    if (own1) *own1 = h->own1;
+    if (row0) *row0 = nxy * h->own0;
+    if (row1) *row1 = nxy * h->own1;
+    if (entry0) *entry0 = row_start(h->geom, 0, 0, h->own0);
+    if (entry1) *entry1 = h->own1 == h->nz ? h->nnz : row_start(h->geom, 0, 0, h->own1);
+    return TPFA_OK;
+}
+
+int tpfa_slab_exchange(tpfa_handle lower, void* p_lower_dev, tpfa_handle upper, void* p_upper_dev, void* stream) {
+    int rc = check_handle(lower);
+    if (rc) return rc;
+    rc = check_handle(upper);
+    if (rc) return rc;
+    if (!lower->slab || !upper->slab || lower->slab_k1 != upper->slab_k0 || lower->slab_nz != upper->slab_nz ||
+        lower->nx != upper->nx || lower->ny != upper->ny || lower->prec != upper->prec)
+        return fail(TPFA_ERR_INVALID_ARG, "slab exchange: the handles are not adjacent slabs of one grid");
+    if (!p_lower_dev || !p_upper_dev) return fail(TPFA_ERR_INVALID_ARG, "slab exchange: NULL pressure array");
+    const size_t plane = lower->real_size * (size_t)lower->nx * (size_t)lower->ny;
+    char* pl = static_cast<char*>(p_lower_dev);
+    char* pu = static_cast<char*>(p_upper_dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DeviceGuard dg(upper->device);
+    // the lower slab's last owned plane -> the upper slab's bottom halo (its plane 0);
+    // the upper slab's first owned plane -> the lower slab's top halo (its last plane)
+    cudaError_t e = cudaMemcpyPeerAsync(pu, upper->device, pl + plane * (size_t)(lower->own1 - 1), lower->device,
+                                        plane, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyPeerAsync(pl + plane * (size_t)lower->own1, lower->device, pu + plane * (size_t)upper->own0,
+                                upper->device, plane, st);
+    if (e != cudaSuccess) return cuda_fail(e, "slab exchange");
     return TPFA_OK;
 }
 
@@ -1411,6 +1507,7 @@ int tpfa_create_ensemble(tpfa_ensemble* out, int M, const tpfa_handle* grids) {
         if (grids[m]->geom.diag != grids[0]->geom.diag || grids[m]->crk != grids[0]->crk)
             return fail(TPFA_ERR_INVALID_ARG, "grid %d differs from grid 0 in connectivity or in c_r == 0", m);
         if (grids[m]->device != grids[0]->device) return fail(TPFA_ERR_INVALID_ARG, "grid %d is on another device", m);
+        if (grids[m]->slab) return fail(TPFA_ERR_INVALID_ARG, "grid %d is a slab handle", m);
     }
     tpfa_ensemble e = new tpfa_ensemble_s();
     e->device = grids[0]->device;

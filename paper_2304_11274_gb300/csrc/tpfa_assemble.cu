@@ -48,7 +48,7 @@ static cudaError_t launch_naive_t(const GridGeom& g, const typename PhysOf<Real>
     return cudaGetLastError();
 }
 
-// Planes [k0, k1) of the grid (k0 a multiple of W); the whole grid by default.
+// Planes [k0, k1) of the grid; the whole grid by default.
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
 static cudaError_t launch_ymarch_w(const GridGeom& g, const typename PhysOf<Real>::type& q,
                                    const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int k0, int k1,
@@ -58,7 +58,7 @@ static cudaError_t launch_ymarch_w(const GridGeom& g, const typename PhysOf<Real
     if (e != cudaSuccess) return e;
     dim3 block(32, W, 1);
     dim3 grid((g.nx + 31) / 32, (g.ny + JY - 1) / JY, (k1 - k0 + W - 1) / W);
-    k_assemble_ymarch<Real, DIAG, CRK, JAC, W><<<grid, block, smem, st>>>(g, q, f, o, JY, k0 / W);
+    k_assemble_ymarch<Real, DIAG, CRK, JAC, W><<<grid, block, smem, st>>>(g, q, f, o, JY, k0, k1);
     return cudaGetLastError();
 }
 
@@ -81,7 +81,7 @@ static cudaError_t launch_xmarch_f(const GridGeom& g, const PhysF& q, const AsmF
     if (e != cudaSuccess) return e;
     dim3 block(32, W, 1);
     dim3 grid((g.nx + 63) / 64, (g.ny + JY - 1) / JY, (k1 - k0 + W - 1) / W);
-    k_assemble_xmarch<DIAG, CRK, W, FAST><<<grid, block, smem, st>>>(g, q, f, o, JY, k0 / W);
+    k_assemble_xmarch<DIAG, CRK, W, FAST><<<grid, block, smem, st>>>(g, q, f, o, JY, k0, k1);
     return cudaGetLastError();
 }
 
@@ -118,7 +118,7 @@ static cudaError_t dispatch(AsmKernel kern, const GridGeom& g, const typename Ph
                             int k1, cudaStream_t st) {
     const bool jac = o.vals != nullptr;
     if (k1 < 0 || k1 > g.nz) k1 = g.nz;
-    if (k0 < 0 || k0 % W != 0 || k0 >= k1) k0 = 0;  // only W-aligned plane ranges are split
+    if (k0 < 0 || k0 >= k1) k0 = 0;
     if (kern == AsmKernel::Naive) {
         if (crk) return jac ? launch_naive_t<Real, true, true>(g, q, f, o, st) : launch_naive_t<Real, true, false>(g, q, f, o, st);
         return jac ? launch_naive_t<Real, false, true>(g, q, f, o, st) : launch_naive_t<Real, false, false>(g, q, f, o, st);
@@ -171,7 +171,7 @@ cudaError_t launch_assemble_mixed_tma(const GridGeom& g, const PhysF& q, bool cr
                                       int k0, int k1) {
     const bool jac = o.vals != nullptr;
     if (k1 < 0 || k1 > g.nz) k1 = g.nz;
-    if (k0 < 0 || k0 % W != 0 || k0 >= k1) k0 = 0;  // the same plane ranges as the per-lane march
+    if (k0 < 0 || k0 >= k1) k0 = 0;
     if (g.diag) {
         if (crk) return jac ? launch_tma_t<true, true, true>(g, q, f, o, maps, JY, k0, k1, st)
                             : launch_tma_t<true, true, false>(g, q, f, o, maps, JY, k0, k1, st);

@@ -16,8 +16,9 @@ struct PhysD;
 enum class AsmKernel { Naive, YMarch, YMarchTma, XMarch };
 
 // JY: rows per warp march; W: warps (z-planes) per block, 4 or 8.  The tiled
-// kernel may be restricted to the planes [k0, k1) (k0 a multiple of W; rows
-// outside are neither read as outputs nor written); the default is the grid.
+// kernels may be restricted to the planes [k0, k1) (rows outside are not
+// written; their cells are still read as neighbours); the default is the
+// grid.  The naive kernel always covers the grid.
 cudaError_t launch_assemble_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk,
                                   const AsmFields<float>& f, const AsmOut<float>& o, int JY, int W,
                                   cudaStream_t st, int k0 = 0, int k1 = -1);

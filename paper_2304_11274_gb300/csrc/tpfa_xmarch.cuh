@@ -571,11 +571,11 @@ struct XState {
 template <bool DIAG, bool CRK, int W, bool FAST>
 __device__ __forceinline__ void xmarch_tile(const GridGeom& g, const PhysF& q, const AsmFields<float>& f,
                                             const AsmOut<float>& o, int JY, int bx, int by, int bz,
-                                            unsigned char* smem) {
+                                            unsigned char* smem, int kbase = 0, int kend = -1) {
     using X = XMarch<DIAG, CRK, W>;
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int k = bz * W + w;
-    if (k >= g.nz) return;  // warp-uniform
+    const int k = kbase + bz * W + w;  // planes [kbase, kend) of the grid (all by default)
+    if (k >= (kend < 0 ? g.nz : kend)) return;  // warp-uniform
     XState<DIAG, CRK, W, FAST> M(g, q, f, o, reinterpret_cast<float*>(smem) + w * X::smem_floats_per_warp(), lane,
                                  k, bx);
     const int j0 = by * JY;
@@ -611,9 +611,9 @@ __device__ __forceinline__ void xmarch_tile(const GridGeom& g, const PhysF& q, c
 
 template <bool DIAG, bool CRK, int W, bool FAST>
 __global__ void __launch_bounds__(32 * W, W == 4 ? 3 : 1)
-    k_assemble_xmarch(GridGeom g, PhysF q, AsmFields<float> f, AsmOut<float> o, int JY, int bz0) {
+    k_assemble_xmarch(GridGeom g, PhysF q, AsmFields<float> f, AsmOut<float> o, int JY, int k0, int k1) {
     extern __shared__ __align__(16) unsigned char smem[];
-    xmarch_tile<DIAG, CRK, W, FAST>(g, q, f, o, JY, blockIdx.x, blockIdx.y, bz0 + (int)blockIdx.z, smem);
+    xmarch_tile<DIAG, CRK, W, FAST>(g, q, f, o, JY, blockIdx.x, blockIdx.y, blockIdx.z, smem, k0, k1);
 }
 
 }  // namespace tpfa

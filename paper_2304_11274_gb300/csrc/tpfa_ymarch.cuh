@@ -778,12 +778,12 @@ constexpr int ymarch_smem_bytes() {
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
 __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename PhysOf<Real>::type& q,
                                             const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int bx, int by,
-                                            int bz, unsigned char* smem) {
+                                            int bz, unsigned char* smem, int kbase = 0, int kend = -1) {
     using M_t = YMarch<Real, DIAG, CRK, JAC, W>;
     constexpr int BUF = 32 * NSLOT + 16 / (int)sizeof(Real);
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int k = bz * W + w;
-    if (k >= g.nz) return;  // warp-uniform
+    const int k = kbase + bz * W + w;  // planes [kbase, kend) of the grid (all by default)
+    if (k >= (kend < 0 ? g.nz : kend)) return;  // warp-uniform
     // per warp: two staging buffers, then the input ring, then the m^n ring
     Real* stage = reinterpret_cast<Real*>(smem) + w * 2 * BUF;
     Real* ring = reinterpret_cast<Real*>(smem) + W * 2 * BUF + w * M_t::RING * M_t::NF * 32;
@@ -953,9 +953,9 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
 template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
 __global__ void __launch_bounds__(32 * W, (sizeof(Real) == 4 ? 16 : 8) / W)
     k_assemble_ymarch(GridGeom g, typename PhysOf<Real>::type q, AsmFields<Real> f, AsmOut<Real> o, int JY,
-                      int bz0) {
+                      int k0, int k1) {
     extern __shared__ __align__(16) unsigned char smem[];
-    ymarch_tile<Real, DIAG, CRK, JAC, W>(g, q, f, o, JY, blockIdx.x, blockIdx.y, bz0 + (int)blockIdx.z, smem);
+    ymarch_tile<Real, DIAG, CRK, JAC, W>(g, q, f, o, JY, blockIdx.x, blockIdx.y, blockIdx.z, smem, k0, k1);
 }
 
 }  // namespace tpfa

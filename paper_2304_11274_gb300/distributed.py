@@ -1,9 +1,12 @@
 """Host-side helpers for running the assembly on several GPUs (one process each).
 
-The assembly has no exchange step between independent problems: an ensemble
-is split across ranks model by model, and a single grid runs as one replica
-per rank.  Only the timing reduction crosses ranks (a max of one scalar), so
-nothing here is on the data path.
+An ensemble is split across ranks model by model (no exchange: the models
+are independent).  One grid is split into z-slabs (api.Slab): before each
+assembly every rank sends its first and last owned planes of pressure to the
+neighbouring ranks and receives their boundary planes into its halo planes,
+point to point (NCCL on GPUs, gloo on CPU); in-plane links never cross a
+slab boundary, so that one plane each way is the whole exchange.  The
+timing reduction (a max of one scalar) also crosses ranks.
 """
 from __future__ import annotations
 
@@ -40,3 +43,25 @@ def aggregate(local_cells: int, local_seconds: float, device=None):
     dist.all_reduce(cells, op=dist.ReduceOp.SUM)
     dist.all_reduce(secs, op=dist.ReduceOp.MAX)
     return int(cells.item()), float(secs.item())
+
+
+def slab_halo_exchange(p, nxy: int, k0: int, k1: int, e0: int, e1: int, rank: int, world: int, group=None):
+    """Fill the halo planes of this rank's slab pressure from the neighbouring
+    ranks.  p holds the planes [e0, e1) of the grid (flattened, nxy values
+    per plane) of slab [k0, k1) (api.slab_bounds(nz, world, rank)); rank r
+    owns slab r.  Sends the first owned plane down and the last owned plane
+    up, receives the neighbours' into planes e0 (below) and e1 - 1 (above);
+    returns after every transfer completed."""
+    import torch.distributed as dist
+
+    plane = lambda k: p[(k - e0) * nxy:(k - e0 + 1) * nxy]
+    ops = []
+    if rank > 0:
+        ops.append(dist.P2POp(dist.isend, plane(k0), rank - 1, group))
+        ops.append(dist.P2POp(dist.irecv, plane(k0 - 1), rank - 1, group))
+    if rank < world - 1:
+        ops.append(dist.P2POp(dist.isend, plane(k1 - 1), rank + 1, group))
+        ops.append(dist.P2POp(dist.irecv, plane(k1), rank + 1, group))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
