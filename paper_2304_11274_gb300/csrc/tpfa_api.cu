@@ -106,6 +106,7 @@ struct tpfa_grid {
     void* T[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // Tx, Ty, Tz, Tpp, Tmp
     void* z = nullptr;
     void* kperm = nullptr;  // permeability in the field type (adjoint)
+    float2* vsplit = nullptr;  // the mixed adjoint's cotangent as FP32 pairs (allocated on first use)
     LinkGeo lg{};           // distance / area per link direction (adjoint)
     double* phi0_d = nullptr;
     void* phi0_r = nullptr;  // phi0 in the field type (mixed path with c_r != 0)
@@ -174,6 +175,8 @@ struct tpfa_grid {
         for (auto& t : T) dev_free(t), t = nullptr;
         dev_free(z);
         dev_free(kperm);
+        dev_free(vsplit);
+        vsplit = nullptr;
         dev_free(phi0_d);
         dev_free(phi0_r);
         dev_free(mn);
@@ -788,9 +791,16 @@ int tpfa_vjp_kernel(tpfa_handle h, tpfa_kernel kern, const double* v_dev, double
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
+    if (h->prec == TPFA_MIXED && !h->vsplit) {
+        if (dev_alloc((void**)&h->vsplit, sizeof(float2) * (size_t)h->N) != cudaSuccess) {
+            cudaGetLastError();
+            h->vsplit = nullptr;
+            return fail(TPFA_ERR_OOM, "device allocation failed for the adjoint's workspace");
+        }
+    }
     if (h->prec == TPFA_MIXED)
         e = launch_vjp_mixed(k, h->geom, h->qf, h->crk, fields_of<float>(h), (const float*)h->kperm, h->lg, v_dev,
-                             g_p_dev, g_lnk_dev, h->status, march_rows(h), h->W, st);
+                             h->vsplit, g_p_dev, g_lnk_dev, h->status, march_rows(h), h->W, st);
     else
         e = launch_vjp_fp64(h->geom, h->qd, h->crk, fields_of<double>(h), (const double*)h->kperm, v_dev, g_p_dev,
                             g_lnk_dev, h->status, st);

@@ -63,9 +63,10 @@ cudaError_t launch_prev_mass_f64(const SetupPhys& s, const double* pn, const dou
 struct LinkGeo;
 // The mixed path's adjoint runs the y-march (JY rows per march, W warps per
 // block) or its naive gather twin; lg: distance over area per link direction.
+// vsplit: N float2 of workspace for the cotangent's FP32 pairs.
 cudaError_t launch_vjp_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
-                             const float* kperm, const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
-                             unsigned int* status, int JY, int W, cudaStream_t st);
+                             const float* kperm, const LinkGeo& lg, const double* v, float2* vsplit, double* g_p,
+                             double* g_lnk, unsigned int* status, int JY, int W, cudaStream_t st);
 cudaError_t launch_vjp_fp64(const GridGeom& g, const PhysD& q, bool crk, const AsmFields<double>& f,
                             const double* kperm, const double* v, double* g_p, double* g_lnk,
                             unsigned int* status, cudaStream_t st);

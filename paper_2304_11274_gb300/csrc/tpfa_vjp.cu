@@ -23,10 +23,12 @@
 //   g_lnk[i] = sum_L F_iL Upsilon_iL (d/A)_iL / (2 k_i) (v_i - v_L)
 // where delta_iL = dF_iL/dp_i + dF_Li/dp_i vanishes except at a tie.  Each v
 // is split into an FP32 pair hi + lo, and v_i - v_L = (hi_i - hi_L) + (lo_i -
-// lo_L) is formed in FP32 (for the two vertical links: in FP64, then
-// narrowed), so each term is accurate relative to itself (a smooth v loses
-// nothing); the terms are FP32 products Kahan-summed in FP32 in slot order
-// and combined in FP64.  Two kernels give identical bits: the y-march of the
+// lo_L) is formed in FP32, so each term is accurate relative to itself (a
+// smooth v loses nothing); the pairs are formed once per call by a pre-pass
+// (k_split_pairs), which keeps the FP64 unit out of the march.  The terms
+// are FP32 products Kahan-summed in FP32 in slot order, then the cell's own
+// term v_i dA_i/dp_i (one FP32 fused product of the pair), combined in
+// FP64.  Two kernels give identical bits: the y-march of the
 // assembly (its adjoint mode, the production kernel) and a
 // one-thread-per-cell gather with checked loads.
 #include <cuda_runtime.h>
@@ -45,7 +47,7 @@ template <typename T>
 __device__ __forceinline__ T ld_chk(const T* p, long long idx, long long N, unsigned int* status) {
     if (p == nullptr || idx < 0 || idx >= N) {
         atomicOr(status, STATUS_DEVICE_CHECK);
-        return T(0);
+        return T{};
     }
     return __ldg(p + idx);
 }
@@ -144,7 +146,7 @@ __device__ __forceinline__ float geo_of(const LinkGeo& lg, int s) {
 template <bool CRK>
 __device__ __forceinline__ void vjp_row(const GridGeom& g, const PhysF& q, const AsmFields<float>& f,
                                         const float* __restrict__ kperm, const LinkGeo& lg,
-                                        const double* __restrict__ v, double* __restrict__ g_p,
+                                        const float2* __restrict__ v, double* __restrict__ g_p,
                                         double* __restrict__ g_lnk, unsigned int* status, int i, int j, int k) {
     const int nx = g.nx, nxy = nx * g.ny;
     const int c = i + nx * j + nxy * k;
@@ -152,8 +154,8 @@ __device__ __forceinline__ void vjp_row(const GridGeom& g, const PhysF& q, const
     const unsigned mask = slot_mask(g, i, j, k);
     const int off[NSLOT] = {-nxy, -nx - 1, -nx, -nx + 1, -1, 0, 1, nx - 1, nx, nx + 1, nxy};
     const CellVal<float> me = make_cell(q, ld_chk(f.p, c, NN, status), ld_chk(f.z, c, NN, status));
-    const double vi = ld_chk(v, c, NN, status);
-    const F2Split si = split_f2(vi);
+    const float2 vi = ld_chk(v, c, NN, status);
+    const F2Split si{vi.x, vi.y};
     const float ki = ld_chk(kperm, c, NN, status);
     const float inv2k = ki > 0.f ? __fdiv_rn(0.5f, ki) : 0.f;
     Kahan32 kp, kk;
@@ -179,20 +181,20 @@ __device__ __forceinline__ void vjp_row(const GridGeom& g, const PhysF& q, const
         const float T = ld_chk(Tp, ti, NN, status);
         const CellVal<float> nb = make_cell(q, ld_chk(f.p, d, NN, status), ld_chk(f.z, d, NN, status));
         const LinkOut<float> L = link(q, T, me, nb);
-        const double vl = ld_chk(v, d, NN, status);
-        const bool vertical = s == 0 || s == 10;
-        const F2Split sl = split_f2(vl);
-        const float dv = vertical ? narrow_rz(__dadd_rn(vi, -vl)) : diff_f2(si, sl);
+        const float2 vl = ld_chk(v, d, NN, status);
+        const F2Split sl{vl.x, vl.y};
+        const float dv = diff_f2(si, sl);
         const float ratio = __fmul_rn(__fmul_rn(T, geo_of(lg, s)), inv2k);
         kp.add(__fmul_rn(L.Da, dv));
         kk.add(__fmul_rn(__fmul_rn(L.F, ratio), dv));
         const float dLK = link(q, T, nb, me).Db;
-        const double vL = vertical ? vl : __dadd_rn(widen(sl.hi), widen(sl.lo));
+        const double vL = __dadd_rn(widen(sl.hi), widen(sl.lo));
         corr = __fma_rn(vL, widen(__fadd_rn(L.Da, dLK)), corr);
     }
     const AccF acc = accumulation<CRK>(q, me.p, ld_chk(f.pn, c, NN, status), ld_chk(f.mn, c, NN, status), me.rho,
                                        CRK ? ld_chk(f.phi0, c, NN, status) : 0.f);
-    const double gp = __dadd_rn(__fma_rn(vi, widen(acc.dA), __dadd_rn(widen(kp.s), -widen(kp.c))), corr);
+    kp.add(__fmaf_rn(si.hi, acc.dA, __fmul_rn(si.lo, acc.dA)));
+    const double gp = __dadd_rn(__dadd_rn(widen(kp.s), -widen(kp.c)), corr);
     const double gk = __dadd_rn(widen(kk.s), -widen(kk.c));
     g_p[c] = gp;
     if (g_lnk) g_lnk[c] = gk;
@@ -202,7 +204,7 @@ __device__ __forceinline__ void vjp_row(const GridGeom& g, const PhysF& q, const
 template <bool CRK>
 __global__ void __launch_bounds__(256) k_vjp_mixed(GridGeom g, PhysF q, AsmFields<float> f,
                                                    const float* __restrict__ kperm, LinkGeo lg,
-                                                   const double* __restrict__ v, double* __restrict__ g_p,
+                                                   const float2* __restrict__ v, double* __restrict__ g_p,
                                                    double* __restrict__ g_lnk, unsigned int* status) {
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
@@ -220,7 +222,7 @@ constexpr int vjp_smem_bytes() {
 template <bool DIAG, bool CRK, int W>
 __global__ void __launch_bounds__(32 * W, 16 / W)
     k_vjp_ymarch(GridGeom g, PhysF q, AsmFields<float> f, AsmOut<float> o, const float* __restrict__ kperm,
-                 LinkGeo lg, const double* __restrict__ v, double* __restrict__ g_p, double* __restrict__ g_lnk,
+                 LinkGeo lg, const float2* __restrict__ v, double* __restrict__ g_p, double* __restrict__ g_lnk,
                  int JY) {
     using M_t = YMarch<float, DIAG, CRK, false, W, false, true>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
     M.ring = ring;
     M.ringm = ringm;
     M.ringw = ringw;
-    M.wv = v;
+    M.wv = reinterpret_cast<const double*>(v);  // 8-byte entries: the pairs (hi, lo)
     M.kperm = kperm;
     M.lg = lg;
     M.gP = g_p;
@@ -270,8 +272,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         const YRow<float> N = M.row_cells(s1);
         const YV vN = M.v_row(s1);
         const YIn<float> D = M.read_in(s0);
-        const double* Wz = ringw + s0 * (M_t::NW * 32) + lane;
-        const double vd = Wz[0], vzm = Wz[64], vzp = Wz[96];
+        const F2Split vzm = M.v_at(s0, 2), vzp = M.v_at(s0, 3);
         const float kC = ring[s0 * (M_t::NF * 32) + M_t::F_K * 32 + lane];
         const int st = s0;
         s0 = s1;
@@ -280,11 +281,11 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         const bool injk = zint && j > 0 && j + 1 < M.ny;
         bool fix;
         if (injk && M.xint)
-            U = M.template row_vjp<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC, fix);
+            U = M.template row_vjp<2>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vzm, vzp, kC, fix);
         else if (injk)
-            U = M.template row_vjp<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC, fix);
+            U = M.template row_vjp<1>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vzm, vzp, kC, fix);
         else
-            U = M.template row_vjp<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vd, vzm, vzp, kC, fix);
+            U = M.template row_vjp<0>(j, P, C, N, D, U, Ty_prev, Tpp_prev, Tmp_prev, vP, vC, vN, vzm, vzp, kC, fix);
         if (fix) fix_rows |= 1ull << (j - j0);
         Ty_prev = D.Ty;
         Tpp_prev = D.Tpp;
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
 
 template <bool DIAG, bool CRK, int W>
 cudaError_t launch_vjp_ymarch_w(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const float* kperm,
-                                const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
+                                const LinkGeo& lg, const float2* v, double* g_p, double* g_lnk,
                                 unsigned int* status, int JY, cudaStream_t st) {
     constexpr int smem = vjp_smem_bytes<W>();
     const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(&k_vjp_ymarch<DIAG, CRK, W>), smem);
@@ -318,7 +319,7 @@ cudaError_t launch_vjp_ymarch_w(const GridGeom& g, const PhysF& q, const AsmFiel
 
 template <bool DIAG, bool CRK>
 cudaError_t launch_vjp_ymarch_t(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const float* kperm,
-                                const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
+                                const LinkGeo& lg, const float2* v, double* g_p, double* g_lnk,
                                 unsigned int* status, int JY, int W, cudaStream_t st) {
     if (W == 8) return launch_vjp_ymarch_w<DIAG, CRK, 8>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
     return launch_vjp_ymarch_w<DIAG, CRK, 4>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
@@ -337,9 +338,26 @@ static cudaError_t launch_vjp_t(const GridGeom& g, const typename PhysOf<Real>::
     return cudaGetLastError();
 }
 
+// The cotangent as FP32 pairs: v = hi + lo with hi the truncation of v and lo
+// the remainder truncated (F2Split), one pair per cell.
+__global__ void k_split_pairs(const double* __restrict__ v, float2* __restrict__ out, long long n) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const F2Split t = split_f2(v[c]);
+        out[c] = make_float2(t.hi, t.lo);
+    }
+}
+
 cudaError_t launch_vjp_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, bool crk, const AsmFields<float>& f,
-                             const float* kperm, const LinkGeo& lg, const double* v, double* g_p, double* g_lnk,
-                             unsigned int* status, int JY, int W, cudaStream_t st) {
+                             const float* kperm, const LinkGeo& lg, const double* v_dbl, float2* vsplit, double* g_p,
+                             double* g_lnk, unsigned int* status, int JY, int W, cudaStream_t st) {
+    {
+        const long long n = (long long)g.nx * g.ny * g.nz;
+        const long long b = (n + 255) / 256;
+        k_split_pairs<<<(unsigned)(b < (1LL << 30) ? (b > 0 ? b : 1) : (1LL << 30)), 256, 0, st>>>(v_dbl, vsplit, n);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const float2* v = vsplit;
     if (kern == AsmKernel::Naive) {
         dim3 block(32, 8, 1);
         dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);

@@ -424,11 +424,14 @@ struct YMarch {
         return r;
     }
 
-    // v of the row in ring slot sl, split (own and halo).
-    __device__ __forceinline__ YV v_row(int sl) const {
-        const double* Wr = ringw + sl * (NW * 32) + lane;
-        return YV{split_f2(Wr[0]), split_f2(Wr[32])};
+    // v of the row in ring slot sl as FP32 pairs (own and halo): in the
+    // adjoint mode the ring's 8-byte entries hold the pairs (hi, lo) of the
+    // split cotangent, not doubles.
+    __device__ __forceinline__ F2Split v_at(int sl, int e) const {
+        const float2 t = reinterpret_cast<const float2*>(ringw + sl * (NW * 32) + lane)[32 * e];
+        return F2Split{t.x, t.y};
     }
+    __device__ __forceinline__ YV v_row(int sl) const { return YV{v_at(sl, 0), v_at(sl, 1)}; }
     __device__ __forceinline__ F2Split v_minus(const YV& v) const {
         F2Split t{__shfl_up_sync(0xffffffffu, v.c.hi, 1), __shfl_up_sync(0xffffffffu, v.c.lo, 1)};
         return lane == 0 ? v.h : t;
@@ -612,10 +615,9 @@ struct YMarch {
     }
 
     // Adjoint of row j (tpfa_vjp.cu states the formulation): vP, vC, vN hold
-    // v of rows j-1, j, j+1 split into FP32 pairs, vd the cell's own v and
-    // vzm, vzp the vertical neighbours' (FP64), kC the cell's k.  Per link,
-    // with dv = v_K - v_L (FP32 from the split pairs; FP64 then narrowed for
-    // the vertical links), the terms dF_KL/dp_K dv and F_KL (k_L / (k_K +
+    // v of rows j-1, j, j+1 split into FP32 pairs, vzm, vzp the vertical
+    // neighbours' pairs, kC the cell's k.  Per link, with dv = v_K - v_L
+    // (FP32 from the split pairs), the terms dF_KL/dp_K dv and F_KL (k_L / (k_K +
     // k_L)) dv share one FP32x2 Kahan sum in slot order; k_L / (k_K + k_L) =
     // Upsilon_KL (d/A) / (2 k_K) for the harmonic two-point transmissibility.
     // The links into row j-1 are reused by negation, which is exact except
@@ -626,7 +628,7 @@ struct YMarch {
     __device__ __forceinline__ YUp<Real> row_vjp(int j, const YRow<Real>& P, const YRow<Real>& C,
                                                  const YRow<Real>& N, const YIn<Real>& D, const YUp<Real>& Uprev,
                                                  Real Ty_prev, Real Tpp_prev, Real Tmp_prev, const YV& vP,
-                                                 const YV& vC, const YV& vN, double vd, double vzm, double vzp,
+                                                 const YV& vC, const YV& vN, const F2Split& vzm, const F2Split& vzp,
                                                  float kC, bool& fix) const {
         const unsigned mask = row_mask<PATH>(j);
         LinkOut<Real> S[NSLOT];
@@ -645,9 +647,7 @@ struct YMarch {
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) {
             if (s == SLOT_SELF || !(mask & (1u << s))) continue;
-            const float dv = s == 0    ? narrow_rz(__dadd_rn(vd, -vzm))
-                             : s == 10 ? narrow_rz(__dadd_rn(vd, -vzp))
-                                       : diff_f2(vC.c, vs[s]);
+            const float dv = diff_f2(vC.c, s == 0 ? vzm : (s == 10 ? vzp : vs[s]));
             const float ratio = __fmul_rn(__fmul_rn(Ts[s], gs[s]), inv2k);
             ks.add(f2(__fmul_rn(S[s].Da, dv), __fmul_rn(__fmul_rn(S[s].F, ratio), dv)));
             zero_flux |= S[s].F == 0.f;
@@ -656,8 +656,12 @@ struct YMarch {
         const AccF acc = accumulation<CRK>(q, C.c.p, D.pn, D.mn, C.c.rho, D.phi0);
         if (act) {
             const int c = kb + nx * j + i;
-            const double gp =
-                __dadd_rn(__fma_rn(vd, widen(acc.dA), __dadd_rn(widen(ks.s.x), -widen(ks.c.x))), 0.0);
+            // the diagonal's own term v_i dA_i/dp_i joins the compensated FP32
+            // sum last; + 0.0 is the twin's tie correction when no link has
+            // zero flux (it turns a -0 into +0 as that addition does)
+            Kahan32 kp{ks.s.x, ks.c.x};
+            kp.add(__fmaf_rn(vC.c.hi, acc.dA, __fmul_rn(vC.c.lo, acc.dA)));
+            const double gp = __dadd_rn(__dadd_rn(widen(kp.s), -widen(kp.c)), 0.0);
             const double gk = __dadd_rn(widen(ks.s.y), -widen(ks.c.y));
             gP[c] = gp;
             if (gK) gK[c] = gk;

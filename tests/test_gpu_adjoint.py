@@ -108,8 +108,9 @@ def test_vjp_every_link_a_tie(precision, kernel):
 
 def test_vjp_smooth_cotangent_keeps_relative_accuracy():
     """v = 1 + 1e-6 u: the permeability gradient depends only on the small
-    differences v_K - v_L, which the mixed path forms in FP64 before
-    narrowing, so its relative error stays at the FP32 level."""
+    differences v_K - v_L, which the mixed path forms from FP32 pairs
+    (hi_K - hi_L) + (lo_K - lo_L), accurate relative to the difference
+    itself, so its relative error stays at the FP32 level."""
     prob = synth.round_to_f32(synth.make_problem(40, 37, 6, seed=27, connectivity=10))
     prob.perm = prob.perm.astype(np.float32).astype(np.float64)
     v = 1.0 + 1e-6 * synth.cotangent(prob.n, seed=10)
