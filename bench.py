@@ -40,9 +40,14 @@ METRIC = "cells/s for TPFA residual+Jacobian (1 GB300) and % of HBM roofline, mi
 SHAPE = (512, 512, 256)
 CONN = 10
 WORKLOAD = "tpfa_residual_jacobian_512x512x256_10pt_mixed"
-KERNEL_SOURCES = ["tpfa_assemble.cu", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
+KERNEL_SOURCES = ["tpfa_assemble.cu", "tpfa_xmarch.cuh", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh",
+                  "tpfa_grid.h"]
 JVP_SOURCES = ["tpfa_jvp.cu", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
 MESH_SOURCES = ["tpfa_mesh.cu", "tpfa_mesh.h", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
+VJP_SOURCES = ["tpfa_vjp.cu", "tpfa_ymarch.cuh", "tpfa_row.cuh", "tpfa_common.cuh", "tpfa_grid.h"]
+# kernel names of the assembly variants, as the launch list shows them
+VARIANT_KERNELS = {"tiled2": "k_assemble_xmarch<DIAG,!CRK,W>", "tiled": "k_assemble_ymarch<float,DIAG,!CR,JAC,W>",
+                   "tiled_tma": "k_assemble_ymarch_tma<DIAG,!CR,JAC,W=4>", "naive": "k_assemble_naive<float,!CR,JAC>"}
 
 
 def env_rank():
@@ -57,49 +62,43 @@ def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-FP64_PEAK_TOPS = 0.625  # nominal GB300 FP64: 1.25 TFLOP/s, i.e. 0.625 T FMA instructions/s
+# FP64 instruction throughput measured on this GPU (CUDA events, one FMA
+# counted once): 604 G/s, 2.0 per clock per SM; a float-to-double conversion
+# issues on the same pipe at the same rate
+FP64_PEAK_TOPS = 0.604
 
 
-def fp64_ops_per_cell(kernel_hash: str):
-    """FP64 instructions per cell of the FP64 assembly kernel, from the
-    committed ncu count, if it was taken on the current kernel source (else
-    None)."""
-    path = os.path.join(ROOT, "profiles", "assemble_fp64_256x256x128_ops.md")
-    if not os.path.exists(path):
-        return None
-    vals = {}
-    with open(path) as fh:
-        for line in fh:
-            if ":" in line and line.strip().startswith("- `"):
-                key, _, v = line.strip()[3:].partition("`:")
-                vals[key.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != kernel_hash:
-        return None
-    try:
-        return float(vals["fp64_ops_per_cell"])
-    except (KeyError, ValueError):
-        return None
-
-
-def profiled_instructions(kernel_hash: str, summary="assemble_mixed_256x256x128_instmix.md"):
-    """Warp instructions issued per cell by the assembly kernel, from the
-    committed ncu instruction-mix summary, if it was taken on the current
-    kernel source (else None)."""
+def profile_values(summary: str, sources=KERNEL_SOURCES) -> dict:
+    """The machine-readable lines (- `key`: `value`) of a committed ncu
+    summary under profiles/, if it was taken on the current source of
+    `sources` (else {}: a figure from another kernel source is not used)."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
-        return None
+        return {}
     vals = {}
     with open(path) as fh:
         for line in fh:
             if ":" in line and line.strip().startswith("- `"):
                 key, _, v = line.strip()[3:].partition("`:")
                 vals[key.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != kernel_hash:
-        return None
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash(sources):
+        return {}
+    return vals
+
+
+def profile_number(vals: dict, key: str):
     try:
-        return float(vals["warp_instructions_per_cell"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def scaled_traffic(vals: dict, cells: int):
+    """DRAM bytes of one launch over `cells` cells, scaled from the summary's
+    bytes per cell (the capture runs a smaller grid of the same kernel: the
+    pool's rule keeps multi-metric captures to small cases), or None."""
+    per_cell = profile_number(vals, "dram_bytes_per_cell")
+    return None if per_cell is None else per_cell * cells
 
 
 def measured_peaks():
@@ -109,26 +108,6 @@ def measured_peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
-
-
-def profiled_traffic(kernel_hash: str, summary="assemble_mixed_512x512x256.md"):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", summary)
-    if not os.path.exists(path):
-        return None
-    vals = {}
-    with open(path) as fh:
-        for line in fh:
-            if ":" in line and line.strip().startswith("- `"):
-                key, _, v = line.strip()[3:].partition("`:")
-                vals[key.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != kernel_hash:
-        return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
 
 
 class ClockSampler:
@@ -384,11 +363,15 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = nbytes / avg_launch_s / 1e9
     khash = kernel_source_hash()
-    tma = args.kernel == "tiled_tma"
+    variant = g.kernel_in_use(args.kernel)
+    # the kernel's ncu summary (a 256 x 256 x 128 capture of the same
+    # variant): warp instructions and DRAM bytes per cell
+    prof = profile_values("assemble_mixed_256x256x128_instmix.md")
+    if prof.get("variant") != variant:
+        prof = {}
     # instruction-issue bound of the same kernel: warp instructions per cell
-    # (ncu) x cells/s against 4 issue slots per SM per clock at the sampled
-    # SM clock
-    ipc = None if tma else profiled_instructions(khash)
+    # x cells/s against 4 issue slots per SM per clock at the sampled SM clock
+    ipc = profile_number(prof, "warp_instructions_per_cell")
     issue_roofline = None
     if ipc is not None:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -397,9 +380,9 @@ def run_ours(args):
         issue_achieved = prob.n / (statistics.mean(launch_ms) * 1e-3) * ipc
         issue_roofline = {"bound": "issue", "warp_instructions_per_cell": ipc, "achieved": issue_achieved / 1e12,
                           "peak": issue_peak / 1e12, "unit": "T warp instructions/s", "frac": issue_achieved / issue_peak,
-                          "source": "ncu count in profiles/assemble_mixed_256x256x128_instmix.md"}
-    kname = "k_assemble_ymarch_tma<DIAG,!CR,JAC,W=4>" if tma else "k_assemble_ymarch<float,DIAG,!CR,JAC>"
-    traffic = profiled_traffic(khash, "assemble_tma_mixed_512x512x256.md" if tma else "assemble_mixed_512x512x256.md")
+                          "source": "ncu count per cell in profiles/assemble_mixed_256x256x128_instmix.md"}
+    kname = VARIANT_KERNELS[variant]
+    traffic = scaled_traffic(prof, prob.n)
 
     # precision of the timed workload: every row of three planes (top,
     # middle, bottom) of the last timed step, against the oracle
@@ -461,14 +444,14 @@ def run_ours(args):
         g64.sync_status()
         f_ms = a.elapsed_time(b) / nf
         b64 = algorithmic_bytes(prob.n, g64.nnz, "fp64")
-        ops = fp64_ops_per_cell(kernel_source_hash())
+        ops = profile_number(profile_values("assemble_fp64_256x256x128_ops.md"), "fp64_ops_per_cell")
         rate = prob.n / (f_ms * 1e-3)
         fp64 = {"value": rate, "unit": "cells/s", "ms_per_step": f_ms,
                 "hbm_GBps": b64 / (f_ms * 1e-3) / 1e9, "hbm_frac": b64 / (f_ms * 1e-3) / 1e9 / peak,
                 "fp64_roofline": None if ops is None else {
                     "bound": "fp64", "ops_per_cell": ops, "achieved": rate * ops / 1e12, "peak": FP64_PEAK_TOPS,
                     "unit": "T FP64 instructions/s", "frac": rate * ops / 1e12 / FP64_PEAK_TOPS,
-                    "peak_kind": "nominal (1.25 TFLOP/s, an FMA counted once)",
+                    "peak_kind": "measured (FP64 FMA instructions/s on this GPU, CUDA events)",
                     "ops_source": "ncu count in profiles/assemble_fp64_256x256x128_ops.md"},
                 "note": "plain FP64 path, same grid; bound by the FP64 pipe, not HBM"}
         g64.close()
@@ -496,11 +479,14 @@ def run_ours(args):
                    "nnz": g.nnz, "precision": "mixed: FP32 flux + Kahan residual, FP64 accumulation/diagonal/R",
                    "l2": "inputs+outputs 6.7 GB per step > 129 MB L2; no flush",
                    "pressure_vectors": len(pres), "parallelism": f"replicas x{world}",
-                   "tiling": {"rows_per_march": tiling[0], "warps_per_block": 4 if tma else tiling[1]},
-                   "kernel_variant": args.kernel},
+                   "tiling": {"rows_per_march": tiling[0],
+                              "warps_per_block": 4 if variant == "tiled_tma" else tiling[1]},
+                   "kernel_variant": variant},
         "issue_roofline": issue_roofline,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
+                     "traffic": traffic, "traffic_source": None if traffic is None else
+                     "ncu DRAM bytes per cell at 256x256x128 (profiles/assemble_mixed_256x256x128_instmix.md) x cells",
+                     "algorithmic_bytes_per_launch": nbytes, "peak_kind": peak_kind,
                      "kernel": kname, "kernel_source_sha256_16": khash},
         "launch_ms": launch_stats,
         "clocks": clk,
@@ -623,11 +609,14 @@ def measure_jvp(g, prob, dev, stream, peak, reps=10):
     nbytes = prob.n * (4 + 4 + 8 + 5 * 4 + 4 + 8 + 8)
     tiling = g.tiling()
     khash = kernel_source_hash(JVP_SOURCES)
+    prof = profile_values("jvp_mixed_256x256x128.md", JVP_SOURCES)
     del w, Jw
     return {"grid": [prob.nx, prob.ny, prob.nz], "value": prob.n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
             "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": nbytes,
-                         "traffic": profiled_traffic(khash, "jvp_mixed_512x512x256.md"),
+                         "traffic": scaled_traffic(prof, prob.n),
+                         "traffic_source": "ncu DRAM bytes per cell at 256x256x128 (profiles/jvp_mixed_256x256x128.md) x cells",
+                         "warp_instructions_per_cell": profile_number(prof, "warp_instructions_per_cell"),
                          "kernel_source_sha256_16": khash},
             "kernel": "k_jvp_ymarch<DIAG,!CR,W=%d>" % tiling[1],
             "tiling": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]},
@@ -666,7 +655,8 @@ def measure_mesh(dev, stream, reps=20):
     out = {"cells": m.n, "connections": m.nc, "nnz": g.nnz, "value": m.n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
            "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": nbytes,
-                        "traffic": profiled_traffic(khash, "mesh_mixed_256x256x128_faulted.md"),
+                        "traffic": profile_number(profile_values("mesh_mixed_256x256x128_faulted.md", MESH_SOURCES),
+                                                  "dram_bytes_per_launch"),
                         "kernel_source_sha256_16": khash},
            "kernel": "k_mesh_assemble<float,!CR,JAC>",
            "workload": "faulted mesh 256x256x128, 10 links + fault NNCs, 5 % inactive, mixed"}
@@ -747,9 +737,14 @@ def measure_adjoint(dev, stream, reps=20):
     # reads p, p^n, depth, k (4 B each), 5 owned T (20 B), m^n and v (8 B each); writes g_p, g_lnk
     nbytes = prob.n * (4 * 4 + 5 * 4 + 8 + 8 + 16)
     peak, _ = measured_peaks()
+    prof = profile_values("vjp_mixed_128x128x128.md", VJP_SOURCES)
     return {"grid": [prob.nx, prob.ny, prob.nz], "value": prob.n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
             "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": nbytes},
+                         "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": nbytes,
+                         "timed": "per call: the cotangent split pre-pass and the march",
+                         "traffic": profile_number(prof, "dram_bytes_per_launch"),
+                         "warp_instructions_per_cell": profile_number(prof, "warp_instructions_per_cell"),
+                         "kernel_source_sha256_16": kernel_source_hash(VJP_SOURCES)},
             "kernel": "k_vjp_ymarch<DIAG,!CR,W=%d>" % tiling[1],
             "tiling": {"rows_per_march": tiling[0], "warps_per_block": tiling[1]},
             "outputs": "g_p and g_lnk (FP64)"}
@@ -1040,7 +1035,7 @@ def main():
                     help="run the z-slab decomposition even on one rank (under torchrun; N > 1 always does)")
     ap.add_argument("--skip-configs", action="store_true",
                     help="skip the per-configuration precision statement and the config 0 / 2 / 4 lines")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "tiled_tma"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "tiled2", "tiled_tma"],
                     help="assembly kernel variant of the timed step (auto = the library's choice)")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
                     help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")

@@ -163,6 +163,16 @@ int tpfa_assemble_jacobian_kernel(tpfa_handle h, tpfa_kernel kern, double* R_dev
                                   double* diag64_dev, void* stream);
 
 /*
+ * The variant a residual + Jacobian call with `kern` runs on this handle in
+ * its current state (AUTO resolved; TILED2 on a grid or fields it does not
+ * accept, and NAIVE on a slab handle, resolved to TILED), written to
+ * *resolved as a tpfa_kernel value.  Launches nothing.  TPFA_ERR_NO_STATE
+ * before tpfa_set_state (the bound pressure's alignment takes part);
+ * TPFA_ERR_INVALID_ARG for TILED_TMA where the assembly call would refuse it.
+ */
+int tpfa_resolve_kernel(tpfa_handle h, tpfa_kernel kern, int* resolved);
+
+/*
  * End-to-end form with HOST buffers (pinned memory recommended): copies the
  * N pressure values in p_host to a library-owned device buffer, binds it as
  * the iterate, assembles, and copies R (N doubles), the CSR values (nnz) and,

@@ -75,6 +75,7 @@ SIGNATURES = [
     ("tpfa_assemble_residual", _I, [_VP, _VP, _VP]),
     ("tpfa_assemble_jacobian", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tpfa_assemble_jacobian_kernel", _I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    ("tpfa_resolve_kernel", _I, [_VP, _I, ctypes.POINTER(_I)]),
     ("tpfa_assemble_jacobian_host", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("tpfa_set_permeability", _I, [_VP, _VP, _VP]),
     ("tpfa_set_log_permeability", _I, [_VP, _VP, _VP]),

@@ -254,6 +254,13 @@ class Grid:
         check(self.lib.tpfa_sync_status(self.handle, _stream(stream)))
 
     # -- tiling
+    def kernel_in_use(self, kernel="auto"):
+        """Name of the variant an assemble_jacobian(kernel=...) call runs on
+        this grid in its current state (the library resolves it)."""
+        out = ctypes.c_int()
+        check(self.lib.tpfa_resolve_kernel(self.handle, _capi.KERNELS[kernel], ctypes.byref(out)))
+        return {v: k for k, v in _capi.KERNELS.items()}[out.value]
+
     def tiling(self):
         jy, w = ctypes.c_int(), ctypes.c_int()
         check(self.lib.tpfa_get_tiling(self.handle, ctypes.byref(jy), ctypes.byref(w)))

@@ -652,6 +652,36 @@ int tpfa_assemble_jacobian_kernel(tpfa_handle h, tpfa_kernel kern, double* R_dev
     return launch(h, k, R_dev, vals_dev, diag64_dev, static_cast<cudaStream_t>(stream));
 }
 
+int tpfa_resolve_kernel(tpfa_handle h, tpfa_kernel kern, int* resolved) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!resolved) return fail(TPFA_ERR_INVALID_ARG, "resolved must be non-NULL");
+    if (!h->has_state) return fail(TPFA_ERR_NO_STATE, "tpfa_set_state has not been called");
+    AsmKernel k;
+    switch (kern) {
+        case TPFA_KERNEL_AUTO: k = auto_kernel(h); break;
+        case TPFA_KERNEL_TILED: k = AsmKernel::YMarch; break;
+        case TPFA_KERNEL_TILED_TMA: k = AsmKernel::YMarchTma; break;
+        case TPFA_KERNEL_TILED2: k = AsmKernel::XMarch; break;
+        case TPFA_KERNEL_NAIVE: k = AsmKernel::Naive; break;
+        default: return fail(TPFA_ERR_INVALID_ARG, "bad kernel variant %d", (int)kern);
+    }
+    // the same fall-backs as launch() and the mixed dispatch
+    if (h->slab && k == AsmKernel::Naive) k = AsmKernel::YMarch;
+    if (k == AsmKernel::YMarchTma && !tma_ready(h))
+        return fail(TPFA_ERR_INVALID_ARG,
+                    "the TMA march needs the mixed path, nx a multiple of 4 and 16-byte aligned p and p^n");
+    if (k == AsmKernel::XMarch && (h->prec != TPFA_MIXED || !xmarch_ok(h->geom, fields_of<float>(h))))
+        k = AsmKernel::YMarch;
+    switch (k) {
+        case AsmKernel::Naive: *resolved = TPFA_KERNEL_NAIVE; break;
+        case AsmKernel::YMarch: *resolved = TPFA_KERNEL_TILED; break;
+        case AsmKernel::YMarchTma: *resolved = TPFA_KERNEL_TILED_TMA; break;
+        case AsmKernel::XMarch: *resolved = TPFA_KERNEL_TILED2; break;
+    }
+    return TPFA_OK;
+}
+
 int tpfa_assemble_jacobian(tpfa_handle h, double* R_dev, void* vals_dev, double* diag64_dev, void* stream) {
     return tpfa_assemble_jacobian_kernel(h, TPFA_KERNEL_AUTO, R_dev, vals_dev, diag64_dev, stream);
 }

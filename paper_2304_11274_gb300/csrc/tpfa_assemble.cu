@@ -106,7 +106,7 @@ static cudaError_t launch_xmarch_t(const GridGeom& g, const PhysF& q, const AsmF
 static bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 // The two-cell march needs nx even and pair-aligned fields.
-static bool xmarch_ok(const GridGeom& g, const AsmFields<float>& f) {
+bool xmarch_ok(const GridGeom& g, const AsmFields<float>& f) {
     return g.nx % 2 == 0 && aligned_to(f.p, 8) && aligned_to(f.pn, 8) && aligned_to(f.z, 8) &&
            aligned_to(f.phi0, 8) && aligned_to(f.Tx, 8) && aligned_to(f.Ty, 8) && aligned_to(f.Tz, 8) &&
            aligned_to(f.Tpp, 8) && aligned_to(f.Tmp, 8) && aligned_to(f.mn, 16);

@@ -34,6 +34,9 @@ cudaError_t launch_assemble_mixed_tma(const GridGeom& g, const PhysF& q, bool cr
                                       const AsmOut<float>& o, const TmaMaps& maps, int JY, int W, cudaStream_t st,
                                       int k0 = 0, int k1 = -1);
 bool tma_grid_ok(const GridGeom& g);
+// Whether the mixed path's fused residual + Jacobian runs the two-cell march
+// on these fields (nx even, pair-aligned fields, 16-byte aligned m^n).
+bool xmarch_ok(const GridGeom& g, const AsmFields<float>& f);
 
 bool tma_encode_state(TmaMaps* m, const GridGeom& g, const float* p, const float* pn);
 bool tma_encode_static(TmaMaps* m, const GridGeom& g, const AsmFields<float>& f, bool crk);

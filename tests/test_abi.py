@@ -109,4 +109,7 @@ def test_null_handle_calls(lib):
     assert lib.tpfa_assemble_residual(None, None, None) == -1
     assert lib.tpfa_sync_status(None, None) == -1
     assert lib.tpfa_get_pattern(None, None, None, None, None) == -1
+    out = ctypes.c_int(-7)
+    assert lib.tpfa_resolve_kernel(None, 0, ctypes.byref(out)) == -1
+    assert out.value == -7
     assert b"handle is NULL" in lib.tpfa_last_error_string()

@@ -106,6 +106,21 @@ def test_kernel_variants_bit_identical(shape, conn, precision, c_r):
 # nx even (the two-cell march's condition): one pair, one exact segment, a
 # segment plus a 2-cell tail, a segment plus a 30-cell tail, several
 # segments with ragged y-runs, single rows and more planes than a block holds.
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_resolved_kernel_follows_the_documented_rule(precision):
+    """AUTO runs TILED2 for mixed grids at least 256 wide with nx even, else
+    TILED; TILED2 on odd nx or the FP64 path runs TILED."""
+    from paper_2304_11274_gb300.api import Grid
+    for shape, auto, two in [((256, 3, 2), "tiled2", "tiled2"), ((254, 3, 2), "tiled", "tiled2"),
+                             ((257, 3, 2), "tiled", "tiled"), ((33, 4, 4), "tiled", "tiled")]:
+        prob = problem(shape, 6, precision, seed=2)
+        with Grid(prob.nx, prob.ny, prob.nz, prob.phys, precision, prob.perm, prob.poro, prob.depth) as g:
+            g.set_state(prob.p, prob.pn)
+            want = (auto, two) if precision == "mixed" else ("tiled", "tiled")
+            assert (g.kernel_in_use("auto"), g.kernel_in_use("tiled2")) == want, shape
+            assert g.kernel_in_use("naive") == "naive" and g.kernel_in_use("tiled") == "tiled"
+
+
 X2_SHAPES = [(2, 3, 2), (64, 5, 3), (66, 9, 5), (94, 7, 4), (128, 66, 9), (130, 41, 11), (256, 1, 6), (6, 70, 1)]
 
 
