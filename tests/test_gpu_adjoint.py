@@ -59,26 +59,32 @@ def test_vjp_matches_oracle(shape, conn, precision, c_r):
         assert _normwise(g_lnk, g_lnk_ref) <= TOL[precision]
 
 
-VARIANT_SHAPES = [(1, 1, 1), (5, 1, 7), (33, 2, 1), (70, 41, 11), (72, 41, 11), (97, 70, 9)]
+# odd and even nx (the two-cell march needs nx even: on odd nx "tiled2"
+# runs the one-cell march), one-row and one-plane grids, x-segments cut by
+# the grid edge, a single 64-cell segment and several
+VARIANT_SHAPES = [(1, 1, 1), (5, 1, 7), (33, 2, 1), (70, 41, 11), (72, 41, 11), (97, 70, 9), (2, 3, 2),
+                  (64, 5, 3), (66, 9, 5), (130, 41, 11), (256, 1, 6), (6, 70, 1)]
 
 
 @pytest.mark.parametrize("shape", VARIANT_SHAPES)
 @pytest.mark.parametrize("conn", [6, 10])
 @pytest.mark.parametrize("c_r", [0.0, 1e-9])
 def test_vjp_kernel_variants_bit_identical(shape, conn, c_r):
-    """The mixed path's adjoint: y-march and naive gather give identical bits
-    under every tiling the autotuner may pick."""
+    """The mixed path's adjoint: the one-cell and two-cell marches and the
+    naive gather give identical bits under every tiling the autotuner may
+    pick."""
     prob = synth.round_to_f32(synth.make_problem(*shape, seed=23, connectivity=conn, c_r=c_r))
     v = synth.cotangent(prob.n, seed=8)
     with _grid(prob, "mixed") as g:
         g.set_state(prob.p, prob.pn)
         gp_n, gk_n = (x.cpu().numpy() for x in g.vjp(v, kernel="naive"))
-        for JY, W in [(16, 4), (32, 8), (64, 4)]:
+        for JY, W in [(16, 4), (32, 8), (64, 4), (7, 4)]:
             g.set_tiling(JY, W)
-            gp_t, gk_t = g.vjp(v, kernel="tiled")
-            g.sync_status()
-            assert np.array_equal(gp_t.cpu().numpy().view(np.uint64), gp_n.view(np.uint64)), (JY, W)
-            assert np.array_equal(gk_t.cpu().numpy().view(np.uint64), gk_n.view(np.uint64)), (JY, W)
+            for kernel in ["tiled", "tiled2", "auto"]:
+                gp_t, gk_t = g.vjp(v, kernel=kernel)
+                g.sync_status()
+                assert np.array_equal(gp_t.cpu().numpy().view(np.uint64), gp_n.view(np.uint64)), (JY, W, kernel)
+                assert np.array_equal(gk_t.cpu().numpy().view(np.uint64), gk_n.view(np.uint64)), (JY, W, kernel)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -200,6 +206,25 @@ def test_vjp_reused_link_ties(conn):
     with _grid(prob, "mixed") as g:
         g.set_state(prob.p, prob.pn)
         a = g.vjp(v, kernel="naive")
-        b = g.vjp(v, kernel="tiled")
-        g.sync_status()
-        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+        for kernel in ["tiled", "tiled2"]:
+            b = g.vjp(v, kernel=kernel)
+            g.sync_status()
+            assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), kernel
+
+
+@pytest.mark.parametrize("conn", [6, 10])
+@pytest.mark.parametrize("shape", [(130, 37, 5), (64, 64, 3)])
+def test_vjp_two_cell_ties_in_every_direction(conn, shape):
+    """Exact ties on x, y and diagonal links, inside a lane's pair of cells,
+    across lanes and across segments: the two-cell adjoint march recomputes
+    those rows and matches the naive gather bit for bit."""
+    prob = C.tie_pairs_problem("mixed", conn, shape=shape)
+    v = synth.cotangent(prob.n, seed=24)
+    with _grid(prob, "mixed") as g:
+        g.set_state(prob.p, prob.pn)
+        a = g.vjp(v, kernel="naive")
+        for tiling in [(32, 4), (5, 8)]:
+            g.set_tiling(*tiling)
+            b = g.vjp(v, kernel="tiled2")
+            g.sync_status()
+            assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), tiling
