@@ -313,6 +313,9 @@ def run_ours(args):
     pn_dev = torch.as_tensor(prob.pn.astype(np.float32), device=dev)
     g.set_state(p_dev[0], pn_dev)
     tiling = g.autotune(None)  # rows per march, warps per block
+    if args.tiling:  # a fixed tiling (profiling a small grid with the large grid's choice)
+        g.set_tiling(*args.tiling)
+        tiling = tuple(args.tiling)
     R, vals, diag = g.empty_outputs()
     stream = torch.cuda.current_stream(dev)
 
@@ -1038,6 +1041,8 @@ def main():
                     help="skip the per-configuration precision statement and the config 0 / 2 / 4 lines")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "tiled2", "tiled_tma"],
                     help="assembly kernel variant of the timed step (auto = the library's choice)")
+    ap.add_argument("--tiling", type=int, nargs=2, default=None, metavar=("ROWS", "WARPS"),
+                    help="fixed tiling of the timed assembly instead of the autotuned one (profiling aid)")
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE),
                     help="grid size (default: the 512 x 512 x 256 workload; smaller shapes are for profiling)")
     args = ap.parse_args()

@@ -1355,7 +1355,7 @@ int log2_bucket(long long n) {
     return b;
 }
 
-const int kTuneJY[] = {16, 32, 64};
+const int kTuneJY[] = {8, 16, 32, 64};
 const int kTuneW[] = {4, 8};
 
 }  // namespace

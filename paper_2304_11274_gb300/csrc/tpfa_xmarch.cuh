@@ -380,6 +380,8 @@ struct XState {
     // whether a reused link of this row met a zero flux (warp-uniform).
     template <int PATH>
     __device__ __forceinline__ bool row(int j, int sD, int sN, int rowbase, float* buf) {
+        // every lane of an interior segment (PATH 2) holds two cells of the grid
+        const bool on = PATH == 2 ? true : act;
         // row j+1's cells and row j's inputs, into registers; then the slot
         // of row j is refilled with row j+2
         CellPair Nc;
@@ -419,7 +421,9 @@ struct XState {
         R.ra = buf + aoff + off_a;
         R.rb = R.ra + len_a;
         // the bulk copy issued from this buffer two steps ago has read it
-        if (v16 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        // (lane 0 issued it; in the other lanes, which have no bulk groups, the
+        // wait returns at once)
+        if (v16) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();
 
         // ---- links and slot values, in slot order
@@ -430,7 +434,7 @@ struct XState {
                 Zm = pair2(a0, b0);
             }
             const Link2 LZM = link_pp(q, tzm, Cc, Zm);
-            R.template put<0>(half(LZM, 0), half(LZM, 1), act);
+            R.template put<0>(half(LZM, 0), half(LZM, 1), on);
         }
         // the segment's halo links: lane 0 -> a's -x (halo of row j) and -x-y
         // (halo of row j-1); lane 31 -> b's +x-y (halo of row j-1)
@@ -443,34 +447,34 @@ struct XState {
         if (DIAG) {
             const float f1 = __shfl_up_sync(0xffffffffu, Uxy.F.y, 1), a1 = __shfl_up_sync(0xffffffffu, Uxy.Da.y, 1),
                         b1 = __shfl_up_sync(0xffffffffu, Uxy.Db.y, 1);
-            R.template put<1>(lane == 0 ? half(LH, 1) : flip(f1, a1, b1), flip(Uxy.F.x, Uxy.Da.x, Uxy.Db.x), act);
+            R.template put<1>(lane == 0 ? half(LH, 1) : flip(f1, a1, b1), flip(Uxy.F.x, Uxy.Da.x, Uxy.Db.x), on);
         }
-        R.template put<2>(flip(Uy.F.x, Uy.Da.x, Uy.Db.x), flip(Uy.F.y, Uy.Da.y, Uy.Db.y), act);
+        R.template put<2>(flip(Uy.F.x, Uy.Da.x, Uy.Db.x), flip(Uy.F.y, Uy.Da.y, Uy.Db.y), on);
         if (DIAG) {
             const float f3 = __shfl_down_sync(0xffffffffu, Umxy.F.x, 1),
                         a3 = __shfl_down_sync(0xffffffffu, Umxy.Da.x, 1),
                         b3 = __shfl_down_sync(0xffffffffu, Umxy.Db.x, 1);
-            R.template put<3>(flip(Umxy.F.y, Umxy.Da.y, Umxy.Db.y), hl ? half(LH, 0) : flip(f3, a3, b3), act);
+            R.template put<3>(flip(Umxy.F.y, Umxy.Da.y, Umxy.Db.y), hl ? half(LH, 0) : flip(f3, a3, b3), on);
         }
         const Link2 LX_ = link_pp(q, Tx, Cc, shift_left(Cc, Cp));
         {
             const float f4 = __shfl_up_sync(0xffffffffu, LX_.F.y, 1), a4 = __shfl_up_sync(0xffffffffu, LX_.Da.y, 1),
                         b4 = __shfl_up_sync(0xffffffffu, LX_.Db.y, 1);
-            R.template put<4>(lane == 0 ? half(LH, 0) : flip(f4, a4, b4), flip(LX_.F.x, LX_.Da.x, LX_.Db.x), act);
+            R.template put<4>(lane == 0 ? half(LH, 0) : flip(f4, a4, b4), flip(LX_.F.x, LX_.Da.x, LX_.Db.x), on);
         }
-        R.template put<6>(half(LX_, 0), half(LX_, 1), act);
+        R.template put<6>(half(LX_, 0), half(LX_, 1), on);
         CellVal<float> Nm, Np;
         neighbours(Nc, Nh, Nm, Np);
         Link2 LMXY, LXY;
         if (DIAG) {
             LMXY = link_pp(q, Tmp, Cc, shift_right(Nm, Nc));
-            R.template put<7>(half(LMXY, 0), half(LMXY, 1), act);
+            R.template put<7>(half(LMXY, 0), half(LMXY, 1), on);
         }
         const Link2 LY = link_pp(q, Ty, Cc, Nc);
-        R.template put<8>(half(LY, 0), half(LY, 1), act);
+        R.template put<8>(half(LY, 0), half(LY, 1), on);
         if (DIAG) {
             LXY = link_pp(q, Tpp, Cc, shift_left(Nc, Np));
-            R.template put<9>(half(LXY, 0), half(LXY, 1), act);
+            R.template put<9>(half(LXY, 0), half(LXY, 1), on);
         }
         {
             CellPair Zp;
@@ -479,14 +483,14 @@ struct XState {
                 Zp = pair2(a1, b1);
             }
             const Link2 LZP = link_pp(q, Tz, Cc, Zp);
-            R.template put<10>(half(LZP, 0), half(LZP, 1), act);
+            R.template put<10>(half(LZP, 0), half(LZP, 1), on);
         }
 
         // ties on this row's reused links: the previous step's up-links and
         // the +x links (a's -x comes from lane-1's b, b's -x from a)
-        const bool tie_x = act && (LX_.F.x == 0.f || (okb && LX_.F.y == 0.f));
+        const bool tie_x = on && (LX_.F.x == 0.f || (okb && LX_.F.y == 0.f));
         const bool tie = __any_sync(0xffffffffu, tie_up || tie_x);
-        tie_up = act && (LY.F.x == 0.f || LY.F.y == 0.f ||
+        tie_up = on && (LY.F.x == 0.f || LY.F.y == 0.f ||
                          (DIAG && (LXY.F.x == 0.f || (okb && LXY.F.y == 0.f) || (oka && LMXY.F.x == 0.f) ||
                                    LMXY.F.y == 0.f)));
 
@@ -501,8 +505,8 @@ struct XState {
         db.add(acc_b.dA);
         const double Da64 = __dadd_rn(widen(da.s), -widen(da.c));
         const double Db64 = __dadd_rn(widen(db.s), -widen(db.c));
-        R.put_diag(__fsub_rn(da.s, da.c), __fsub_rn(db.s, db.c), act);
-        if (act) {
+        R.put_diag(__fsub_rn(da.s, da.c), __fsub_rn(db.s, db.c), on);
+        if (on) {
             const int c = kb + nx * j + ia;
             if (FAST || o.R) {
                 if (r16) *reinterpret_cast<double2*>(o.R + c) = make_double2(Ra, Rb);
@@ -530,13 +534,14 @@ struct XState {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (qhi > qlo) {
-                    if (lane == 0) {
-                        const uint32_t src = (uint32_t)__cvta_generic_to_shared(buf + qlo * 4);
-                        const uint32_t bytes = (uint32_t)(qhi - qlo) * 16u;
-                        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
-                                     "cp.async.bulk.commit_group;" ::"l"(dst + qlo * 4), "r"(src), "r"(bytes)
-                                     : "memory");
-                    }
+                    // issued and committed by lane 0 (a guard predicate, no branch)
+                    const uint32_t src = (uint32_t)__cvta_generic_to_shared(buf + qlo * 4);
+                    const uint32_t bytes = (uint32_t)(qhi - qlo) * 16u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %3, 0;\n\t"
+                                 "@p cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+                                 "@p cp.async.bulk.commit_group;\n\t}" ::"l"(dst + qlo * 4), "r"(src), "r"(bytes),
+                                 "r"(lane)
+                                 : "memory");
                     const int nh = qlo * 4 - aoff, nt = span - qhi * 4;  // each < 4
                     if (lane >= 1 && lane <= nh) dst[aoff + lane - 1] = buf[aoff + lane - 1];
                     if (lane >= 8 && lane < 8 + nt) dst[qhi * 4 + lane - 8] = buf[qhi * 4 + lane - 8];
@@ -612,7 +617,7 @@ __device__ __forceinline__ void xmarch_tile(const GridGeom& g, const PhysF& q, c
         rowbase += M.rowA + axis_links(j, g.ny) * M.rowB;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (M.v16 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (M.v16) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (tie_rows) {  // warp-uniform; every bulk store of the warp has completed
         __syncwarp();
         for (int b = 0; b < 64; ++b)
