@@ -353,8 +353,8 @@ int tpfa_set_tiling(tpfa_handle h, int rows_per_march, int warps_per_block);
 int tpfa_get_tiling(tpfa_handle h, int* rows_per_march, int* warps_per_block);
 
 /*
- * Choose the tiling by timing candidates (rows_per_march 8, 16, 32, 64 x
- * warps_per_block 4, 8) on this grid at its bound state, or take it from
+ * Choose the tiling by timing candidates (rows_per_march 8, 16, 24, 32, 40,
+ * 48, 64 x warps_per_block 4, 8) on this grid at its bound state, or take it from
  * `cache_path` (a text file of "key rows warps" lines, key = device, path,
  * connectivity, porosity law and log2 of the cell count); a new choice is
  * written back.  cache_path may be NULL (no cache).  Allocates and frees

@@ -154,6 +154,14 @@ struct tpfa_grid {
     double* kv_part = nullptr;
     KrylovScalars* kv_S = nullptr;
     KrylovScalars* kv_S_host = nullptr;  // pinned
+    // the solve's batches of iterations as one CUDA graph, launched on a
+    // library stream that follows the caller's stream through events
+    cudaStream_t kv_stream = nullptr;
+    cudaEvent_t kv_ev[2] = {};
+    cudaGraphExec_t kv_exec = nullptr;
+    const double* kv_exec_x = nullptr;  // what the graph was captured for
+    int kv_exec_every = 0;
+    bool kv_exec_line = false;
 
     void release() {
         for (auto& ev : h_ev) {
@@ -172,6 +180,11 @@ struct tpfa_grid {
         dev_free(kv_S);
         if (kv_S_host) cudaFreeHost(kv_S_host);
         kv_vals = nullptr, kv_diag = nullptr, kv_R = nullptr, kv_part = nullptr, kv_S = nullptr, kv_S_host = nullptr;
+        if (kv_exec) cudaGraphExecDestroy(kv_exec);
+        for (auto& ev : kv_ev)
+            if (ev) cudaEventDestroy(ev), ev = nullptr;
+        if (kv_stream) cudaStreamDestroy(kv_stream);
+        kv_exec = nullptr, kv_stream = nullptr;
         for (auto& t : T) dev_free(t), t = nullptr;
         dev_free(z);
         dev_free(kperm);
@@ -380,21 +393,76 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     *Sh = KrylovScalars{};
     Sh->tol2 = rtol * rtol;
     Sh->max_iters = max_iters;
-    cudaError_t e = cudaMemcpyAsync(w.S, Sh, sizeof(KrylovScalars), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = krylov_dinv(h->geom, mixed, h->kv_vals, h->kv_diag, w.dinv, w.lmul, w.up, line, st);
-    if (e == cudaSuccess) e = krylov_start(h->geom, h->N, b, sign, w, st);
+    // The iterations run on the library's stream as CUDA-graph launches of
+    // `every` iterations each (ten kernels per iteration: one launch per
+    // batch instead of ten per iteration); that stream waits for `st`
+    // before the solve and `st` for it after.  A stream that is being
+    // captured gets the plain launches instead.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    bool graph = cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+    if (graph && !h->kv_stream) {
+        graph = cudaStreamCreateWithFlags(&h->kv_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&h->kv_ev[0], cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&h->kv_ev[1], cudaEventDisableTiming) == cudaSuccess;
+        if (!graph) {
+            cudaGetLastError();
+            for (auto& ev : h->kv_ev)
+                if (ev) cudaEventDestroy(ev), ev = nullptr;
+            if (h->kv_stream) cudaStreamDestroy(h->kv_stream), h->kv_stream = nullptr;
+        }
+    }
+    cudaGetLastError();
+    cudaStream_t ks = st;
+    cudaError_t e = cudaSuccess;
+    if (graph) {
+        e = cudaEventRecord(h->kv_ev[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->kv_stream, h->kv_ev[0], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "Krylov stream");
+        ks = h->kv_stream;
+        if (h->kv_exec && (h->kv_exec_x != x || h->kv_exec_every != every || h->kv_exec_line != line)) {
+            cudaGraphExecDestroy(h->kv_exec);
+            h->kv_exec = nullptr;
+        }
+        if (!h->kv_exec) {  // capture one batch of iterations
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamBeginCapture(ks, cudaStreamCaptureModeThreadLocal);
+            cudaError_t el = cudaSuccess;
+            for (int q = 0; q < every && e == cudaSuccess && el == cudaSuccess; ++q)
+                el = krylov_iteration(h->geom, h->N, mixed, h->kv_vals, h->kv_diag, w, line, ks);
+            if (e == cudaSuccess) e = cudaStreamEndCapture(ks, &gr);
+            if (e == cudaSuccess) e = el;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->kv_exec, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            if (e != cudaSuccess) {
+                h->kv_exec = nullptr;
+                return cuda_fail(e, "Krylov graph");
+            }
+            h->kv_exec_x = x;
+            h->kv_exec_every = every;
+            h->kv_exec_line = line;
+        }
+    }
+    e = cudaMemcpyAsync(w.S, Sh, sizeof(KrylovScalars), cudaMemcpyHostToDevice, ks);
+    if (e == cudaSuccess) e = krylov_dinv(h->geom, mixed, h->kv_vals, h->kv_diag, w.dinv, w.lmul, w.up, line, ks);
+    if (e == cudaSuccess) e = krylov_start(h->geom, h->N, b, sign, w, ks);
     if (e != cudaSuccess) return cuda_fail(e, "Krylov start");
     // every kernel returns at entry once `done` is set, so batches of
     // `every` iterations may overshoot the stopping point harmlessly; the
     // device stops at max_iters, so this loop ends after at most
     // max_iters / every + 1 polls
     for (int it = 0; it <= max_iters + every; it += every) {
-        for (int q = 0; q < every && e == cudaSuccess; ++q)
-            e = krylov_iteration(h->geom, h->N, mixed, h->kv_vals, h->kv_diag, w, line, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(Sh, w.S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (graph) e = cudaGraphLaunch(h->kv_exec, ks);
+        for (int q = 0; !graph && q < every && e == cudaSuccess; ++q)
+            e = krylov_iteration(h->geom, h->N, mixed, h->kv_vals, h->kv_diag, w, line, ks);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Sh, w.S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, ks);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ks);
         if (e != cudaSuccess) return cuda_fail(e, "Krylov iteration");
         if (Sh->done) break;
+    }
+    if (graph) {
+        e = cudaEventRecord(h->kv_ev[1], ks);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->kv_ev[1], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "Krylov stream");
     }
     const bool converged = Sh->done && !Sh->breakdown && Sh->rr <= Sh->tol2 * Sh->bb;
     if (stats) {
@@ -1355,7 +1423,7 @@ int log2_bucket(long long n) {
     return b;
 }
 
-const int kTuneJY[] = {8, 16, 32, 64};
+const int kTuneJY[] = {8, 16, 24, 32, 40, 48, 64};
 const int kTuneW[] = {4, 8};
 
 }  // namespace
