@@ -710,7 +710,7 @@ def measure_newton(dev, stream, reps=3):
                                        "achieved": per_iter_bytes / (ms_iter * 1e-3) / 1e9, "peak": peak,
                                        "unit": "GB/s", "frac": per_iter_bytes / (ms_iter * 1e-3) / 1e9 / peak},
             "preconditioner": "z-line (tridiagonal along z, per column)",
-            "note": "includes one assembly and the update; 10 launches per BiCGStab iteration, host poll every 8"}
+            "note": "includes one assembly and the update; 10 kernels per BiCGStab iteration, 8 iterations per CUDA-graph launch and host poll"}
 
 
 def measure_adjoint(dev, stream, reps=20):

@@ -89,6 +89,37 @@ __device__ __forceinline__ void kahan2_masked(Kahan2& k, float2 x, bool va, bool
     k.c.y = vb ? t.c.y : k.c.y;
 }
 
+// accumulation() of Eq. vk for cells a and b at once: each half performs
+// the scalar function's operations in its order (FP32x2 halves round as the
+// scalar instructions do), so the results are its bits.  Returns the FP64
+// terms A of both cells and the pair of dA/dp.
+template <bool CRK>
+__device__ __forceinline__ float2 accumulation2(const PhysF& q, float2 p, float2 pn, double2 mn, float2 rho,
+                                                float2 phi0, double& Aa, double& Ab) {
+    if constexpr (CRK) {
+        const AccF a = accumulation<true>(q, p.x, pn.x, mn.x, rho.x, phi0.x);
+        const AccF b = accumulation<true>(q, p.y, pn.y, mn.y, rho.y, phi0.y);
+        Aa = a.A;
+        Ab = b.A;
+        return f2(a.dA, b.dA);
+    } else {
+        const float2 m1 = f2(-1.f);
+        const float2 x = __fmul2_rn(f2(q.c_f), __ffma2_rn(pn, m1, p));  // c_f (p - p^n)
+        float2 e;
+        if (fabsf(x.x) < 0.0078125f && fabsf(x.y) < 0.0078125f) {  // expm1_f32's series for both
+            float2 r = __ffma2_rn(x, f2(1.f / 24.f), f2(1.f / 6.f));
+            r = __ffma2_rn(x, r, f2(0.5f));
+            r = __ffma2_rn(x, r, f2(1.f));
+            e = __fmul2_rn(r, x);
+        } else {
+            e = f2(expm1_f32(x.x), expm1_f32(x.y));
+        }
+        Aa = __dmul_rn(mn.x, widen(e.x));
+        Ab = __dmul_rn(mn.y, widen(e.y));
+        return __fmul2_rn(__fmul2_rn(f2(q.c_f), f2(narrow_rz(mn.x), narrow_rz(mn.y))), __fadd2_rn(f2(1.f), e));
+    }
+}
+
 template <bool DIAG, bool CRK, int W>
 struct XMarch {
     // ---- ring layout (floats, per warp and slot)
@@ -496,16 +527,16 @@ struct XState {
 
         // ---- accumulation (Eq. vk) and the FP64 combinations
         R.gather();
-        const AccF acc_a = accumulation<CRK>(q, Cc.p.x, pn.x, mn.x, Cc.rho.x, phi.x);
-        const AccF acc_b = accumulation<CRK>(q, Cc.p.y, pn.y, mn.y, Cc.rho.y, phi.y);
-        const double Ra = __dadd_rn(__dadd_rn(acc_a.A, widen(R.kr.s.x)), -widen(R.kr.c.x));
-        const double Rb = __dadd_rn(__dadd_rn(acc_b.A, widen(R.kr.s.y)), -widen(R.kr.c.y));
-        Kahan32 da{R.kd.s.x, R.kd.c.x}, db{R.kd.s.y, R.kd.c.y};
-        da.add(acc_a.dA);
-        db.add(acc_b.dA);
-        const double Da64 = __dadd_rn(widen(da.s), -widen(da.c));
-        const double Db64 = __dadd_rn(widen(db.s), -widen(db.c));
-        R.put_diag(__fsub_rn(da.s, da.c), __fsub_rn(db.s, db.c), on);
+        double Aa, Ab;
+        const float2 dA = accumulation2<CRK>(q, Cc.p, pn, mn, Cc.rho, phi, Aa, Ab);
+        const double Ra = __dadd_rn(__dadd_rn(Aa, widen(R.kr.s.x)), -widen(R.kr.c.x));
+        const double Rb = __dadd_rn(__dadd_rn(Ab, widen(R.kr.s.y)), -widen(R.kr.c.y));
+        Kahan2 dd = R.kd;  // the diagonals: dA joins each compensated sum last
+        dd.add(dA);
+        const double Da64 = __dadd_rn(widen(dd.s.x), -widen(dd.c.x));
+        const double Db64 = __dadd_rn(widen(dd.s.y), -widen(dd.c.y));
+        const float2 dg = __ffma2_rn(dd.c, f2(-1.f), dd.s);  // s - c, the FP32 diagonal values
+        R.put_diag(dg.x, dg.y, on);
         if (on) {
             const int c = kb + nx * j + ia;
             if (FAST || o.R) {
