@@ -1600,7 +1600,7 @@ int tpfa_autotune(tpfa_handle h, const char* cache_path, void* stream) {
             for (int r = 0; r < 2 && !rc; ++r) rc = launch(h, auto_kernel(h), (double*)R, vals, (double*)diag, st);
             if (rc) break;
             cudaEventRecord(a, st);
-            for (int r = 0; r < 3 && !rc; ++r) rc = launch(h, auto_kernel(h), (double*)R, vals, (double*)diag, st);
+            for (int r = 0; r < 5 && !rc; ++r) rc = launch(h, auto_kernel(h), (double*)R, vals, (double*)diag, st);
             cudaEventRecord(b, st);
             e = cudaEventSynchronize(b);
             float ms = 0.f;

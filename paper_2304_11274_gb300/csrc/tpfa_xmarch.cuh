@@ -519,10 +519,12 @@ struct XState {
 
         // ties on this row's reused links: the previous step's up-links and
         // the +x links (a's -x comes from lane-1's b, b's -x from a)
-        const bool tie_x = on && (LX_.F.x == 0.f || (okb && LX_.F.y == 0.f));
+        // (on an interior segment every lane's +x and diagonal links exist)
+        const bool kb2 = PATH == 2 ? true : okb, ka2 = PATH == 2 ? true : oka;
+        const bool tie_x = on && (LX_.F.x == 0.f || (kb2 && LX_.F.y == 0.f));
         const bool tie = __any_sync(0xffffffffu, tie_up || tie_x);
         tie_up = on && (LY.F.x == 0.f || LY.F.y == 0.f ||
-                         (DIAG && (LXY.F.x == 0.f || (okb && LXY.F.y == 0.f) || (oka && LMXY.F.x == 0.f) ||
+                         (DIAG && (LXY.F.x == 0.f || (kb2 && LXY.F.y == 0.f) || (ka2 && LMXY.F.x == 0.f) ||
                                    LMXY.F.y == 0.f)));
 
         // ---- accumulation (Eq. vk) and the FP64 combinations
