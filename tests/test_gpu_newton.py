@@ -190,3 +190,29 @@ def test_linear_solve_adjoint_grid_properties():
         bound = 2 * rtol * float(torch.linalg.norm(bt)) + 4 * 2.0 ** -24 * float(torch.linalg.norm(absJx))
     assert st["converged"] == 1
     assert res <= bound, (res, bound)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_iterations_give_the_same_bits_on_every_stream(precision):
+    """The solve replays its batches of iterations as a CUDA graph on a
+    library stream ordered with the caller's: the solution is the same, bit
+    for bit, on the default stream, on a user stream, with a new solution
+    buffer (a new graph), with another batch size (a new graph) and again
+    after those."""
+    prob = _problem((24, 20, 12), precision, seed=47)
+    b = synth.cotangent(prob.n, seed=48)
+    with _grid(prob, precision) as g:
+        g.set_state(prob.p, prob.pn)
+        x0, st0 = g.linear_solve(b, rtol=1e-10, max_iters=2000)
+        x0 = x0.cpu()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            x1, st1 = g.linear_solve(b, rtol=1e-10, max_iters=2000, stream=s)
+        s.synchronize()
+        assert torch.equal(x1.cpu(), x0) and st1.iterations == st0.iterations
+        x2, _ = g.linear_solve(b, rtol=1e-10, max_iters=2000, out=torch.empty_like(x1))
+        assert torch.equal(x2.cpu(), x0)
+        x3, st3 = g.linear_solve(b, rtol=1e-10, max_iters=2000, check_every=3)
+        assert torch.equal(x3.cpu(), x0) and st3.iterations == st0.iterations
+        x4, _ = g.linear_solve(b, rtol=1e-10, max_iters=2000)
+        assert torch.equal(x4.cpu(), x0)
