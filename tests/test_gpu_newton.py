@@ -209,10 +209,10 @@ def test_batched_iterations_give_the_same_bits_on_every_stream(precision):
         with torch.cuda.stream(s):
             x1, st1 = g.linear_solve(b, rtol=1e-10, max_iters=2000, stream=s)
         s.synchronize()
-        assert torch.equal(x1.cpu(), x0) and st1.iterations == st0.iterations
+        assert torch.equal(x1.cpu(), x0) and st1["iterations"] == st0["iterations"]
         x2, _ = g.linear_solve(b, rtol=1e-10, max_iters=2000, out=torch.empty_like(x1))
         assert torch.equal(x2.cpu(), x0)
         x3, st3 = g.linear_solve(b, rtol=1e-10, max_iters=2000, check_every=3)
-        assert torch.equal(x3.cpu(), x0) and st3.iterations == st0.iterations
+        assert torch.equal(x3.cpu(), x0) and st3["iterations"] == st0["iterations"]
         x4, _ = g.linear_solve(b, rtol=1e-10, max_iters=2000)
         assert torch.equal(x4.cpu(), x0)
