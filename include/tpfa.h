@@ -70,7 +70,8 @@ typedef enum {
 typedef enum {
     TPFA_KERNEL_AUTO = 0,  /* the library's choice: TILED2 for the fused residual
                               + Jacobian of TPFA_MIXED grids it accepts that
-                              are at least 256 cells wide in x, else TILED */
+                              are at least 256 cells wide in x, or exactly
+                              128 or 192 wide, else TILED */
     TPFA_KERNEL_NAIVE = 1, /* one thread per cell, every neighbour read from
                               global memory: the correctness baseline */
     TPFA_KERNEL_TILED = 2, /* a warp per 32-cell x-segment of a z-plane,

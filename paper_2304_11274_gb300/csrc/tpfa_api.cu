@@ -259,18 +259,23 @@ bool tma_ready(tpfa_grid* h) {
     return h->tm_state;
 }
 
-// The library's choice of assembly kernel: on grids at least 256 cells wide
-// the march with two cells per lane (the dispatch runs the one-cell march
-// where that one does not apply: residual-only calls, the FP64 path, odd nx,
-// fields not pair-aligned), else the one-cell march.  The two-cell march's
-// x-boundary rows cost every lane of a boundary segment a masked sum, so it
-// wins only where few segments touch the x boundaries: measured (G cells/s,
-// one-cell vs two-cell, best tiling each) 25.4 vs 24.1 at 128^3, 27.9 vs 24.2
-// at 192 x 160 x 80, 34.8 vs 36.8 at 256^3, 38.0 vs 42.7 at 512 x 512 x 256,
-// 38.4 vs 44.8 at 1024 x 256 x 256.  (The TMA march gives the same bits but
-// measured 8 % slower than the one-cell march at 512 x 512 x 256: its row
-// waits stall where the per-lane prefetch does not.)
-AsmKernel auto_kernel(tpfa_grid* h) { return h->nx >= 256 ? AsmKernel::XMarch : AsmKernel::YMarch; }
+// The library's choice of assembly kernel: the march with two cells per lane
+// on grids at least 256 cells wide, or 128 or 192 wide (whole 64-cell
+// segments), else the one-cell march (the dispatch runs the one-cell march
+// where the two-cell one does not apply: residual-only calls, the FP64 path,
+// odd nx, fields not pair-aligned).  A ragged last segment leaves lanes idle
+// and the x-boundary segments cost their lanes masked sums, so narrow grids
+// whose width is not a multiple of 64 do better one cell per lane: measured
+// (G cells/s, one-cell vs two-cell, best rows per march each) 26.4 vs 28.3 at
+// 128^3, 26.9 vs 24.7 at 160 x 160 x 80, 28.5 vs 29.2 at 192 x 160 x 80, 22.3
+// vs 18.1 at 224 x 96 x 48, 11.5 vs 10.4 at 64^3, 33.4 vs 36.3 at
+// 256 x 256 x 128, 38.0 vs 46.4 at 512 x 512 x 256.  (The TMA march gives the
+// same bits but measured 8 % slower than the one-cell march at
+// 512 x 512 x 256: its row waits stall where the per-lane prefetch does not.)
+AsmKernel auto_kernel(tpfa_grid* h) {
+    const int nx = h->nx;
+    return nx >= 256 || nx == 128 || nx == 192 ? AsmKernel::XMarch : AsmKernel::YMarch;
+}
 
 int launch(tpfa_grid* h, AsmKernel kern, double* R, void* vals, double* diag64, cudaStream_t st, int k0 = 0,
            int k1 = -1) {

@@ -108,11 +108,14 @@ def test_kernel_variants_bit_identical(shape, conn, precision, c_r):
 # segments with ragged y-runs, single rows and more planes than a block holds.
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_resolved_kernel_follows_the_documented_rule(precision):
-    """AUTO runs TILED2 for mixed grids at least 256 wide with nx even, else
-    TILED; TILED2 on odd nx or the FP64 path runs TILED."""
+    """AUTO runs TILED2 for mixed grids at least 256 wide with nx even, or
+    128 or 192 wide, else TILED; TILED2 on odd nx or the FP64 path runs
+    TILED."""
     from paper_2304_11274_gb300.api import Grid
     for shape, auto, two in [((256, 3, 2), "tiled2", "tiled2"), ((254, 3, 2), "tiled", "tiled2"),
-                             ((257, 3, 2), "tiled", "tiled"), ((33, 4, 4), "tiled", "tiled")]:
+                             ((257, 3, 2), "tiled", "tiled"), ((33, 4, 4), "tiled", "tiled"),
+                             ((128, 3, 2), "tiled2", "tiled2"), ((192, 3, 2), "tiled2", "tiled2"),
+                             ((160, 3, 2), "tiled", "tiled2"), ((64, 3, 2), "tiled", "tiled2")]:
         prob = problem(shape, 6, precision, seed=2)
         with Grid(prob.nx, prob.ny, prob.nz, prob.phys, precision, prob.perm, prob.poro, prob.depth) as g:
             g.set_state(prob.p, prob.pn)
