@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W)
         }
         __syncthreads();
         if (s_tile >= total) break;
-        ymarch_tile<float, DIAG, CRK, true, W>(sm.g, sm.q, sm.f, sm.o, JY, s_bx, s_by, s_bz, smem);
+        ymarch_tile<float, DIAG, CRK, true, W, true>(sm.g, sm.q, sm.f, sm.o, JY, s_bx, s_by, s_bz, smem);
         __syncthreads();  // every warp is done with this tile's descriptor and buffers
     }
 }

@@ -779,7 +779,34 @@ constexpr int ymarch_smem_bytes() {
 // One block's work: x-segment bx, y-run by, z-block bz of one grid.  Shared
 // by the single-grid kernel and the persistent ensemble kernel (whose blocks
 // call it once per tile they claim), so both produce identical rows.
-template <typename Real, bool DIAG, bool CRK, bool JAC, int W>
+// Runs step(path, j) over the rows j0 .. j1-1 of a march: the boundary rows
+// (j = 0, j = ny - 1, and every row of a boundary plane) on path 0, the
+// interior rows in one loop whose path is fixed for the warp (2: interior
+// x-segment, 1: a segment at an x boundary) instead of a choice per row.
+// `path` is a std::integral_constant, so the step is compiled per path.
+template <class Step>
+__device__ __forceinline__ void march_rows(int j0, int j1, int ny, bool zint, bool xint, Step&& step) {
+    int j = j0;
+    if (zint) {
+        if (j == 0 && j < j1) step(std::integral_constant<int, 0>{}, j++);
+        const int jend = min(j1, ny - 1);
+        if (xint) {
+#pragma unroll 1
+            for (; j < jend; ++j) step(std::integral_constant<int, 2>{}, j);
+        } else {
+#pragma unroll 1
+            for (; j < jend; ++j) step(std::integral_constant<int, 1>{}, j);
+        }
+    }
+#pragma unroll 1
+    for (; j < j1; ++j) step(std::integral_constant<int, 0>{}, j);
+}
+
+// SPLIT: run the rows through march_rows (one loop per path).  Measured at
+// 160 x 160 x 80 and on the 64-model ensemble: the ensemble's persistent
+// kernel gains 5 % with it, the single-grid kernel loses 4 %, so only the
+// ensemble uses it.
+template <typename Real, bool DIAG, bool CRK, bool JAC, int W, bool SPLIT = false>
 __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename PhysOf<Real>::type& q,
                                             const AsmFields<Real>& f, const AsmOut<Real>& o, int JY, int bx, int by,
                                             int bz, unsigned char* smem, int kbase = 0, int kend = -1) {
@@ -822,26 +849,48 @@ __device__ __forceinline__ void ymarch_tile(const GridGeom& g, const typename Ph
     // exact tie dPhi == 0: recomputed after the march (bit j - j0; JY <= 64)
     unsigned long long tie_rows = 0ull;
 
-    for (int j = j0; j < j1; ++j) {
-        // row j+2 is requested now and used two steps later; row j+1 arrived
-        M.issue_row(j + 2, s2);
-        M.wait_all_but_newest();
-        const YRow<Real> N = M.row_cells(s1);
-        const YIn<Real> D = M.read_in(s0);
-        const int st = s0;
-        s0 = s1;
-        s1 = s2;
-        s2 = st;
-        Real* buf = stage + ((j - j0) & 1) * BUF;
-        M.buffer_ready();
-        if (__any_sync(0xffffffffu, U.tie)) tie_rows |= 1ull << (j - j0);
-        const bool injk = zint && j > 0 && j + 1 < M.ny;
-        if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, buf, rowbase);
-        else if (injk) U = M.template row<1>(j, P, C, N, D, U, buf, rowbase);
-        else U = M.template row<0>(j, P, C, N, D, U, buf, rowbase);
-        rowbase += M.row_base_step(j);
-        P = C;
-        C = N;
+    if constexpr (SPLIT) {
+        march_rows(j0, j1, M.ny, zint, M.xint, [&](auto path, int j) {
+            constexpr int PATH = decltype(path)::value;
+            // row j+2 is requested now and used two steps later; row j+1 arrived
+            M.issue_row(j + 2, s2);
+            M.wait_all_but_newest();
+            const YRow<Real> N = M.row_cells(s1);
+            const YIn<Real> D = M.read_in(s0);
+            const int st = s0;
+            s0 = s1;
+            s1 = s2;
+            s2 = st;
+            Real* buf = stage + ((j - j0) & 1) * BUF;
+            M.buffer_ready();
+            if (__any_sync(0xffffffffu, U.tie)) tie_rows |= 1ull << (j - j0);
+            U = M.template row<PATH>(j, P, C, N, D, U, buf, rowbase);
+            rowbase += M.row_base_step(j);
+            P = C;
+            C = N;
+        });
+    } else {
+        for (int j = j0; j < j1; ++j) {
+            // row j+2 is requested now and used two steps later; row j+1 arrived
+            M.issue_row(j + 2, s2);
+            M.wait_all_but_newest();
+            const YRow<Real> N = M.row_cells(s1);
+            const YIn<Real> D = M.read_in(s0);
+            const int st = s0;
+            s0 = s1;
+            s1 = s2;
+            s2 = st;
+            Real* buf = stage + ((j - j0) & 1) * BUF;
+            M.buffer_ready();
+            if (__any_sync(0xffffffffu, U.tie)) tie_rows |= 1ull << (j - j0);
+            const bool injk = zint && j > 0 && j + 1 < M.ny;
+            if (injk && M.xint) U = M.template row<2>(j, P, C, N, D, U, buf, rowbase);
+            else if (injk) U = M.template row<1>(j, P, C, N, D, U, buf, rowbase);
+            else U = M.template row<0>(j, P, C, N, D, U, buf, rowbase);
+            rowbase += M.row_base_step(j);
+            P = C;
+            C = N;
+        }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     M.drain();
