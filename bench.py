@@ -876,6 +876,27 @@ def oracle_rates(prob, kind="assemble", v=None):
     return out
 
 
+def oracle_rates_sum(probs, sample):
+    """Oracle cells/s over several grids (total cells / total time),
+    single-threaded and on every thread."""
+    import oracle
+    allt = oracle.max_threads()
+    out = {}
+    for label, n in (("threads_1", 1), ("threads_all", allt)):
+        oracle.set_threads(n)
+        cells, sec = 0, 0.0
+        for prob in probs:
+            pat = oracle.pattern(prob.nx, prob.ny, prob.nz, prob.phys["connectivity"])
+            t, _ = time_oracle(lambda: oracle.assemble(prob.nx, prob.ny, prob.nz, prob.phys, prob.perm, prob.poro,
+                                                       prob.depth, prob.p, prob.pn, pat=pat), min_reps=1, min_s=0.2)
+            cells += prob.n
+            sec += t
+        out[label] = {"value": cells / sec, "unit": "cells/s", "threads": n}
+    oracle.set_threads(allt)
+    out["sample"] = sample
+    return out
+
+
 def gpu_rate(g, p_dev, R, vals, diag, calls, stream, dev):
     """Cells/s of the fused assembly on a bound grid (CUDA events)."""
     import torch
@@ -963,8 +984,19 @@ def measure_configs(dev, stream, full=True):
         "oracle": oracle_rates(synth.round_to_f32(synth.make_problem(128, 128, 16, synth.BASE_SEED + 4,
                                                                      connectivity=10)), kind="vjp",
                                v=synth.cotangent(128 * 128 * 16, seed=5))}
+    # config 1 on the host: a 4-plane slab of the 512 x 512 x 256 workload
+    out["config1_512x512x256_10pt_mixed"] = {
+        "oracle": oracle_rates(synth.round_to_f32(synth.make_problem(512, 512, 4, synth.BASE_SEED + 1,
+                                                                     connectivity=CONN)))}
+    # config 3 on the host: the sum over a sample of the ensemble's models
+    shapes = synth.ensemble_shapes()
+    sample = [0, len(shapes) // 3, 2 * len(shapes) // 3, len(shapes) - 1]
+    probs = [synth.round_to_f32(synth.make_problem(*shapes[m], synth.BASE_SEED + 1000 + m, connectivity=CONN))
+             for m in sample]
     out["config3_ensemble"] = {"note": "each model's rows are bit-identical to its single-grid assembly "
-                                       "(tests/test_gpu_ensemble.py), so its error is config 1's"}
+                                       "(tests/test_gpu_ensemble.py), so its error is config 1's",
+                               "oracle": oracle_rates_sum(probs, "models %s of the 64 (%d cells)" %
+                                                          (sample, sum(q.n for q in probs)))}
     return out
 
 
