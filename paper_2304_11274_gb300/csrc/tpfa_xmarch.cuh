@@ -153,6 +153,15 @@ __device__ __forceinline__ void cpa4(float* dst, const float* src, bool valid) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
 }
+// A 4-byte copy issued only by the lanes where `lane_on` holds (a guard
+// predicate, so the warp does not branch around it).
+__device__ __forceinline__ void cpa4_if(float* dst, const float* src, bool valid, bool lane_on) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
+                 "@q cp.async.ca.shared.global [%0], [%1], 4, %2;\n\t}" ::"r"(d),
+                 "l"(src), "r"(valid ? 4 : 0), "r"((unsigned)lane_on)
+                 : "memory");
+}
 __device__ __forceinline__ void cpa16(void* dst, const void* src, bool valid) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
@@ -327,17 +336,18 @@ struct XState {
         cpa8(Sl + X::P_PZP * 64, f.p + cp, a && zp);
         cpa8(Sl + X::P_ZZP * 64, f.z + cp, a && zp);
         cpa16(S + X::OFF_MN + 4 * lane, f.mn + c, a);
-        if (lane == 0 || hl) {
+        {  // the halo cells: lanes 0 and 31 only, under a guard predicate
+            const bool hlane = lane == 0 || hl;
             float* H = S + X::OFF_H + (hl ? 1 : 0);
             const int ch = kb + nx * (rv ? r : 0) + (hact ? ih : 0);
-            cpa4(H + 0, f.p + ch, rv && hact);
-            cpa4(H + 2, f.z + ch, rv && hact);
+            cpa4_if(H + 0, f.p + ch, rv && hact, hlane);
+            cpa4_if(H + 2, f.z + ch, rv && hact, hlane);
             // lane 0: Tx(i0-1, r) and Tpp(i0-1, r-1); lane 31: Tmp(i0+64, r-1)
             const bool t1 = rv && hact && !hl;
-            cpa4(H + 4, f.Tx + (t1 ? ch : 0), t1);
+            cpa4_if(H + 4, f.Tx + (t1 ? ch : 0), t1, hlane);
             if (DIAG) {
                 const bool t2 = rv && hact && r > 0;
-                cpa4(H + 6, (hl ? f.Tmp : f.Tpp) + (t2 ? ch - nx : 0), t2);
+                cpa4_if(H + 6, (hl ? f.Tmp : f.Tpp) + (t2 ? ch - nx : 0), t2, hlane);
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -549,8 +559,12 @@ struct XState {
                 if (r16) *reinterpret_cast<double2*>(o.diag64 + c) = make_double2(Da64, Db64);
                 else o.diag64[c] = Da64, o.diag64[c + 1] = Db64;
             }
-            if (nonfinite(Ra) || nonfinite(Rb) || nonfinite(Da64) || nonfinite(Db64))
-                atomicOr(o.status, STATUS_NONFINITE);
+            // a non-finite value has an all-ones exponent: one test for the four
+            const uint32_t ex = max(max((uint32_t)__double2hiint(Ra) & 0x7ff00000u,
+                                        (uint32_t)__double2hiint(Rb) & 0x7ff00000u),
+                                    max((uint32_t)__double2hiint(Da64) & 0x7ff00000u,
+                                        (uint32_t)__double2hiint(Db64) & 0x7ff00000u));
+            if (ex == 0x7ff00000u) atomicOr(o.status, STATUS_NONFINITE);
         }
 
         // ---- the segment's CSR values: one bulk copy (ends by single lanes)

@@ -286,14 +286,21 @@ def test_transmissibility_matches_oracle(conn):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_nonfinite_pressure_is_reported(precision):
+@pytest.mark.parametrize("shape,kernel", [((8, 8, 4), "auto"), ((128, 6, 4), "tiled2"), ((130, 6, 4), "tiled2")])
+@pytest.mark.parametrize("bad", [37, -1, np.inf])
+def test_nonfinite_pressure_is_reported(precision, shape, kernel, bad):
+    """A NaN or infinite pressure, inside the grid or at its last cell,
+    with the one-cell and the two-cell marches."""
     from paper_2304_11274_gb300.api import TPFAError
-    prob = problem((8, 8, 4), 10, precision)
+    prob = problem(shape, 10, precision)
     p = prob.p.copy()
-    p[37] = np.nan
+    if bad == np.inf:
+        p[prob.n // 2] = np.inf
+    else:
+        p[bad] = np.nan
     with _grid(prob, precision) as g:
         g.set_state(p, prob.pn)
-        g.assemble_jacobian()
+        g.assemble_jacobian(kernel=kernel)
         with pytest.raises(TPFAError) as ei:
             g.sync_status()
         assert ei.value.name == "TPFA_ERR_NONFINITE"
