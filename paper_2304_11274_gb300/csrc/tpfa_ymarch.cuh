@@ -725,8 +725,10 @@ struct YMarch {
 
     // Wait until the bulk store issued from this buffer two steps ago has
     // read it (lane 0 issued it), so the buffer can be refilled.
+    // (every lane waits: the other lanes have no bulk groups, so their wait
+    // returns at once, and the warp does not branch)
     __device__ __forceinline__ void buffer_ready() const {
-        if (JAC && v16 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        if (JAC && v16) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();
     }
 
@@ -742,11 +744,13 @@ struct YMarch {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (qhi > qlo) {
-                if (lane == 0) {
+                {  // issued and committed by lane 0 (a guard predicate, no branch)
                     const uint32_t src = (uint32_t)__cvta_generic_to_shared(buf + qlo * VEC);
                     const uint32_t bytes = (uint32_t)(qhi - qlo) * 16u;
-                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
-                                 "cp.async.bulk.commit_group;" ::"l"(dst + qlo * VEC), "r"(src), "r"(bytes)
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %3, 0;\n\t"
+                                 "@p cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+                                 "@p cp.async.bulk.commit_group;\n\t}" ::"l"(dst + qlo * VEC), "r"(src), "r"(bytes),
+                                 "r"(lane)
                                  : "memory");
                 }
                 const int nh = qlo * VEC - aoff, nt = span - qhi * VEC;  // each < VEC
