@@ -403,10 +403,16 @@ typedef struct {
  * Solve J x = b, J the Jacobian at the bound state (assembled into
  * library-owned workspace by this call), x0 = 0.  b_dev, x_dev: N doubles
  * (device, caller-owned).  opts may be NULL (defaults); stats may be NULL.
- * Synchronous on `stream`.  Returns TPFA_ERR_NO_CONVERGENCE when the
+ * Synchronous on `stream`: the iterations run after the work already queued
+ * on `stream`, and the call returns once they are done.  They run on a
+ * library-owned stream of the handle (it waits for `stream` before the solve
+ * and `stream` waits for it after), each batch of check_every iterations as
+ * one launch of a CUDA graph captured on the first solve into x_dev (and
+ * again when x_dev or check_every change); a `stream` that is itself being
+ * captured gets plain launches.  Returns TPFA_ERR_NO_CONVERGENCE when the
  * tolerance was not met (x_dev then holds the last iterate).  The first
  * call allocates the workspace: nnz values, 12 FP64 vectors of N (and, on
- * TPFA_MIXED, four FP32 vectors).
+ * TPFA_MIXED, four FP32 vectors), and creates the stream and two events.
  */
 int tpfa_linear_solve(tpfa_handle h, const double* b_dev, double* x_dev, const tpfa_krylov_opts* opts,
                       tpfa_krylov_stats* stats, void* stream);
