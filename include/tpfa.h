@@ -575,6 +575,33 @@ int tpfa_assemble_jacobian_static(int nx, int ny, int nz, const tpfa_params* prm
 long long tpfa_static_workspace_bytes(int nx, int ny, int nz, int connectivity, tpfa_precision prec,
                                       int rock_compressible);
 
+/*
+ * The library's own exponentials, evaluated element-wise so that they can be
+ * checked against CUDA's exp / expm1 / expm1f over an argument sweep.  Eq.
+ * density's exp(c_f (p - p_ref)) takes exp_fp64 on the FP64 path, and the
+ * accumulation term of Eq. vk, written with expm1(c_f (p - p^n)), takes
+ * expm1_fp64 on the FP64 path and expm1_f32 in the FP32 kernels.  Below
+ * |x| < 2^-5 (FP64) and |x| < 2^-7 (FP32) they are Taylor series in Horner
+ * form; larger arguments, NaN and infinities go to CUDA's exp / expm1 /
+ * expm1f.
+ *
+ *   fn    : which routine (TPFA_MATH_EXPM1_FP32 rounds each x to FP32
+ *           first; its FP32 result is widened exactly)
+ *   x_dev : n doubles (device, caller-owned, read only)
+ *   y_dev : n doubles (device, caller-owned), written
+ *   n     : number of arguments; 0 launches nothing
+ *   stream: cudaStream_t as void*; asynchronous on it
+ *
+ * TPFA_ERR_INVALID_ARG for an unknown fn, n < 0, or a NULL pointer with
+ * n > 0.  A test and diagnostics entry point: no assembly call needs it.
+ */
+typedef enum {
+    TPFA_MATH_EXP_FP64 = 0,
+    TPFA_MATH_EXPM1_FP64 = 1,
+    TPFA_MATH_EXPM1_FP32 = 2
+} tpfa_math_fn;
+int tpfa_math_eval(tpfa_math_fn fn, const double* x_dev, double* y_dev, long long n, void* stream);
+
 /* Free everything the handle owns; NULL-safe.  Synchronises the device. */
 int tpfa_destroy(tpfa_handle h);
 

@@ -116,6 +116,7 @@ SIGNATURES = [
     ("tpfa_destroy_ensemble", _I, [_VP]),
     ("tpfa_assemble_jacobian_static", _I, [_I, _I, _I, ctypes.POINTER(TPFAParams), _I] + [_VP] * 10),
     ("tpfa_static_workspace_bytes", _LL, [_I, _I, _I, _I, _I, _I]),
+    ("tpfa_math_eval", _I, [_I, _VP, _VP, _LL, _VP]),
     ("tpfa_destroy", _I, [_VP]),
     ("tpfa_last_error_string", ctypes.c_char_p, []),
     ("tpfa_version", _I, []),

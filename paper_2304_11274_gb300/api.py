@@ -285,6 +285,20 @@ def slab_bounds(nz, parts, part):
     return tuple(x.value for x in v)
 
 
+MATH_FNS = {"exp_fp64": 0, "expm1_fp64": 1, "expm1_f32": 2}
+
+
+def math_eval(fn: str, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """The library's exponential `fn` ("exp_fp64", "expm1_fp64" or
+    "expm1_f32") of every element of x, as FP64 on x's device
+    (tpfa_math_eval)."""
+    lib = _capi.load()
+    x = x.to(dtype=torch.float64).contiguous()
+    y = torch.empty_like(x)
+    check(lib.tpfa_math_eval(MATH_FNS[fn], _ptr(x), _ptr(y), x.numel(), _stream(stream)))
+    return y
+
+
 class Slab(Grid):
     """Planes [k0, k1) of an nx x ny x nz grid with one halo plane on each
     side that exists (a z-slab of a decomposition over GPUs; Section 5's

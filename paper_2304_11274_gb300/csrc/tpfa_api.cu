@@ -600,6 +600,17 @@ int tpfa_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 
 const char* tpfa_last_error_string(void) { return g_err.c_str(); }
 
+int tpfa_math_eval(tpfa_math_fn fn, const double* x_dev, double* y_dev, long long n, void* stream) {
+    g_err.clear();
+    if (fn != TPFA_MATH_EXP_FP64 && fn != TPFA_MATH_EXPM1_FP64 && fn != TPFA_MATH_EXPM1_FP32)
+        return fail(TPFA_ERR_INVALID_ARG, "bad math function %d", (int)fn);
+    if (n < 0) return fail(TPFA_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > 0 && (!x_dev || !y_dev)) return fail(TPFA_ERR_INVALID_ARG, "x and y must be non-NULL");
+    const cudaError_t e = launch_math_eval((int)fn, x_dev, y_dev, n, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "math launch");
+    return TPFA_OK;
+}
+
 int tpfa_create_grid(tpfa_handle* out, int nx, int ny, int nz, const tpfa_params* prm, tpfa_precision prec,
                      const double* perm_dev, const double* poro_dev, const double* depth_dev, void* stream) {
     g_err.clear();

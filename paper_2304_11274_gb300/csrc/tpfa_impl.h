@@ -130,4 +130,7 @@ cudaError_t ensure_smem_limit(const void* func, int bytes);
 // CSR pattern (row_ptr int64 N+1, col_idx int32 nnz).
 cudaError_t launch_pattern(const GridGeom& g, long long* row_ptr, int* col_idx, cudaStream_t st);
 
+// y[i] = the library exponential `fn` (a tpfa_math_fn) of x[i], i < n.
+cudaError_t launch_math_eval(int fn, const double* x, double* y, long long n, cudaStream_t st);
+
 }  // namespace tpfa

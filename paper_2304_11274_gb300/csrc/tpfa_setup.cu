@@ -68,6 +68,20 @@ __global__ void k_store_perm(const double* __restrict__ perm, Real* out, long lo
         out[c] = (Real)perm_at<LOG>(perm, c);
 }
 
+// The library's own exponentials, one argument per element: exp_fp64,
+// expm1_fp64, and expm1_f32 of the argument rounded to FP32 (its result
+// widened exactly).  Only tpfa_math_eval launches it.
+__global__ void k_math_eval(int fn, const double* __restrict__ x, double* __restrict__ y, long long n) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double a = x[c];
+        double r;
+        if (fn == TPFA_MATH_EXP_FP64) r = exp_fp64(a);
+        else if (fn == TPFA_MATH_EXPM1_FP64) r = expm1_fp64(a);
+        else r = (double)expm1_f32(__double2float_rn(a));
+        y[c] = r;
+    }
+}
+
 Geo make_geo(const SetupPhys& s) {
     Geo q;
     q.ax = s.dy * s.dz / s.dx;
@@ -187,6 +201,12 @@ cudaError_t launch_prev_mass_f64(const SetupPhys& s, const double* pn, const dou
 cudaError_t launch_pattern(const GridGeom& g, long long* row_ptr, int* col_idx, cudaStream_t st) {
     const long long N = (long long)g.nx * g.ny * g.nz;
     k_pattern<<<blocks_for(N), kThreads, 0, st>>>(g, row_ptr, col_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_math_eval(int fn, const double* x, double* y, long long n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_math_eval<<<blocks_for(n), kThreads, 0, st>>>(fn, x, y, n);
     return cudaGetLastError();
 }
 

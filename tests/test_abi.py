@@ -102,6 +102,19 @@ def test_mesh_arguments_rejected_before_any_device_work(lib):
     assert lib.tpfa_mesh_sync_status(None, None) == -1
 
 
+def test_math_eval_argument_checks(lib):
+    """Rejected before any launch; n = 0 launches nothing."""
+    buf = ctypes.c_double(0.0)
+    assert lib.tpfa_math_eval(3, ctypes.byref(buf), ctypes.byref(buf), 1, None) == -1
+    assert b"bad math function" in lib.tpfa_last_error_string()
+    assert lib.tpfa_math_eval(-1, ctypes.byref(buf), ctypes.byref(buf), 1, None) == -1
+    assert lib.tpfa_math_eval(0, ctypes.byref(buf), ctypes.byref(buf), -1, None) == -1
+    assert lib.tpfa_math_eval(1, None, ctypes.byref(buf), 4, None) == -1
+    assert lib.tpfa_math_eval(2, ctypes.byref(buf), None, 4, None) == -1
+    assert lib.tpfa_math_eval(2, None, None, 0, None) == 0
+    assert lib.tpfa_last_error_string() == b""
+
+
 def test_null_handle_calls(lib):
     assert lib.tpfa_destroy(None) == 0
     assert lib.tpfa_set_state(None, None, None, None) == -1
