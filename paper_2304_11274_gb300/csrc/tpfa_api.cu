@@ -419,6 +419,15 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     cudaGetLastError();
     cudaStream_t ks = st;
     cudaError_t e = cudaSuccess;
+    // `st` waits for the library stream on every return after the fork, the
+    // error returns included, so that nothing the caller queues next on `st`
+    // overlaps iterations still in flight
+    auto join = [&]() -> cudaError_t {
+        if (ks == st) return cudaSuccess;
+        cudaError_t j = cudaEventRecord(h->kv_ev[1], ks);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(st, h->kv_ev[1], 0);
+        return j;
+    };
     if (graph) {
         e = cudaEventRecord(h->kv_ev[0], st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->kv_stream, h->kv_ev[0], 0);
@@ -440,6 +449,7 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
             if (gr) cudaGraphDestroy(gr);
             if (e != cudaSuccess) {
                 h->kv_exec = nullptr;
+                join();
                 return cuda_fail(e, "Krylov graph");
             }
             h->kv_exec_x = x;
@@ -450,7 +460,10 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
     e = cudaMemcpyAsync(w.S, Sh, sizeof(KrylovScalars), cudaMemcpyHostToDevice, ks);
     if (e == cudaSuccess) e = krylov_dinv(h->geom, mixed, h->kv_vals, h->kv_diag, w.dinv, w.lmul, w.up, line, ks);
     if (e == cudaSuccess) e = krylov_start(h->geom, h->N, b, sign, w, ks);
-    if (e != cudaSuccess) return cuda_fail(e, "Krylov start");
+    if (e != cudaSuccess) {
+        join();
+        return cuda_fail(e, "Krylov start");
+    }
     // every kernel returns at entry once `done` is set, so batches of
     // `every` iterations may overshoot the stopping point harmlessly; the
     // device stops at max_iters, so this loop ends after at most
@@ -461,14 +474,14 @@ int krylov_solve(tpfa_grid* h, const double* b, double sign, double* x, const tp
             e = krylov_iteration(h->geom, h->N, mixed, h->kv_vals, h->kv_diag, w, line, ks);
         if (e == cudaSuccess) e = cudaMemcpyAsync(Sh, w.S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, ks);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ks);
-        if (e != cudaSuccess) return cuda_fail(e, "Krylov iteration");
+        if (e != cudaSuccess) {
+            join();
+            return cuda_fail(e, "Krylov iteration");
+        }
         if (Sh->done) break;
     }
-    if (graph) {
-        e = cudaEventRecord(h->kv_ev[1], ks);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->kv_ev[1], 0);
-        if (e != cudaSuccess) return cuda_fail(e, "Krylov stream");
-    }
+    e = join();
+    if (e != cudaSuccess) return cuda_fail(e, "Krylov stream");
     const bool converged = Sh->done && !Sh->breakdown && Sh->rr <= Sh->tol2 * Sh->bb;
     if (stats) {
         stats->iterations = Sh->iter;
