@@ -590,10 +590,12 @@ long long tpfa_static_workspace_bytes(int nx, int ny, int nz, int connectivity, 
  *   x_dev : n doubles (device, caller-owned, read only)
  *   y_dev : n doubles (device, caller-owned), written
  *   n     : number of arguments; 0 launches nothing
- *   stream: cudaStream_t as void*; asynchronous on it
+ *   stream: cudaStream_t as void*; asynchronous on it, on the current
+ *           device (x_dev and y_dev must live there)
  *
  * TPFA_ERR_INVALID_ARG for an unknown fn, n < 0, or a NULL pointer with
- * n > 0.  A test and diagnostics entry point: no assembly call needs it.
+ * n > 0; TPFA_ERR_CUDA if the launch fails.  A test and diagnostics entry
+ * point: no assembly call needs it.
  */
 typedef enum {
     TPFA_MATH_EXP_FP64 = 0,
