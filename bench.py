@@ -163,6 +163,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_link_gbs(dev, nbytes=1 << 30, reps=3):
+    """Copy bandwidth (GB/s) between pinned host memory and this GPU, each
+    direction alone: one 1 GiB cudaMemcpyAsync, best of `reps`.  The
+    end-to-end call copies its outputs back every step, so the device-to-host
+    figure bounds it."""
+    import torch
+
+    n = nbytes // 4
+    d = torch.ones(n, dtype=torch.float32, device=dev)
+    h = torch.empty(n, dtype=torch.float32).pin_memory()
+    out = {}
+    for name, fn in (("d2h", lambda: h.copy_(d, non_blocking=True)), ("h2d", lambda: d.copy_(h, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize(dev)
+        best = float("inf")
+        for _ in range(reps):
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize(dev)
+            best = min(best, time.perf_counter() - t)
+        out[name] = nbytes / best / 1e9
+    del d, h
+    return out
+
+
 def algorithmic_bytes(n, nnz, precision, crk=False):
     """Bytes one assembly must move at least: each input field read once, each
     output written once (halo re-reads excluded: they are cache traffic)."""
@@ -421,6 +446,15 @@ def run_ours(args):
                "h2d_bytes_per_step": prob.n * 4, "d2h_bytes_per_step": prob.n * 8 + g.nnz * 4 + prob.n * 8,
                "steps": e2e_steps, "api": "tpfa_assemble_jacobian_host (pinned host buffers)"}
         del ph, Rh, vh, dh
+        # the host link: the outputs' copy back bounds the call (the two
+        # directions and the assembly overlap in its pipeline)
+        link = host_link_gbs(dev)
+        t_step = float(es.item()) / e2e_steps
+        d2h = e2e["d2h_bytes_per_step"] / t_step / 1e9
+        e2e["host_link"] = {"bound": "d2h", "achieved": d2h, "peak": link["d2h"], "unit": "GB/s",
+                            "frac": d2h / link["d2h"], "h2d_peak": link["h2d"],
+                            "ceiling_cells_per_s": cells / (e2e["d2h_bytes_per_step"] / (link["d2h"] * 1e9)),
+                            "peak_measured": "this run: one 1 GiB pinned copy per direction, best of 3"}
 
     jvp = None if args.skip_jvp else measure_jvp(g, prob, dev, stream, peak)
 
