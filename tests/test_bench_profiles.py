@@ -61,3 +61,16 @@ def test_source_hash_covers_the_two_cell_march():
     """The headline kernel's hash changes with the two-cell march's source."""
     assert "tpfa_xmarch.cuh" in bench.KERNEL_SOURCES
     assert bench.kernel_source_hash() != bench.kernel_source_hash(bench.FP64_SOURCES)
+
+
+def test_algorithmic_bytes_of_the_headline_workload():
+    """The roofline's numerator on 512 x 512 x 256 with 10 links: reads of
+    p, p^n (FP32), m^n (FP64), five owned transmissibilities and depth
+    (FP32), 40 B per cell; writes of R and diag64 (FP64) and one FP32 value
+    per CSR entry (736,101,376 entries, the pattern's closed form)."""
+    n, nnz = 512 * 512 * 256, 736101376
+    assert bench.algorithmic_bytes(n, nnz, "mixed") == 40 * n + 16 * n + 4 * nnz == 6702501888
+    # c_r != 0 adds the FP32 phi0 read
+    assert bench.algorithmic_bytes(n, nnz, "mixed", crk=True) == 6702501888 + 4 * n
+    # FP64: every field and value 8 bytes, no separate diagonal
+    assert bench.algorithmic_bytes(n, nnz, "fp64") == 72 * n + 8 * n + 8 * nnz
