@@ -864,17 +864,28 @@ def plane_errors(prob, precision, planes, R, vals, diag):
     return worst
 
 
-def host_info():
-    cpu = ""
+# Arm core names by the "CPU part" field of /proc/cpuinfo (implementer 0x41)
+ARM_PARTS = {"0xd0c": "Arm Neoverse N1", "0xd40": "Arm Neoverse V1", "0xd49": "Arm Neoverse N2",
+             "0xd4f": "Arm Neoverse V2"}
+
+
+def host_info(cpuinfo="/proc/cpuinfo"):
+    """Host threads and CPU model (x86: the model name; Arm, which has no
+    model name line: the core named from its part number)."""
+    fields = {}
     try:
-        with open("/proc/cpuinfo") as fh:
+        with open(cpuinfo) as fh:
             for line in fh:
-                if line.lower().startswith(("model name", "cpu part", "hardware")):
-                    cpu = line.split(":", 1)[1].strip()
-                    break
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
     except OSError:
         pass
-    return {"nproc": os.cpu_count(), "cpu_model": cpu or os.uname().machine}
+    cpu = fields.get("model name") or fields.get("hardware") or ""
+    part = fields.get("cpu part", "")
+    if not cpu and part:
+        cpu = f"{ARM_PARTS.get(part.lower(), 'Arm core')} (CPU part {part})"
+    return {"nproc": os.cpu_count(), "cpu_model": cpu or os.uname().machine, "machine": os.uname().machine}
 
 
 def time_oracle(fn, min_reps=3, min_s=0.5):

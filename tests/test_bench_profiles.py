@@ -74,3 +74,15 @@ def test_algorithmic_bytes_of_the_headline_workload():
     assert bench.algorithmic_bytes(n, nnz, "mixed", crk=True) == 6702501888 + 4 * n
     # FP64: every field and value 8 bytes, no separate diagonal
     assert bench.algorithmic_bytes(n, nnz, "fp64") == 72 * n + 8 * n + 8 * nnz
+
+
+def test_host_info_names_the_cpu(tmp_path):
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU architecture: 8\n"
+                   "CPU variant\t: 0x0\nCPU part\t: 0xd4f\nCPU revision\t: 0\n\nprocessor\t: 1\nCPU part\t: 0xd4f\n")
+    assert bench.host_info(str(arm))["cpu_model"] == "Arm Neoverse V2 (CPU part 0xd4f)"
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nvendor_id\t: GenuineIntel\nmodel name\t: Some CPU @ 2.00GHz\n")
+    assert bench.host_info(str(x86))["cpu_model"] == "Some CPU @ 2.00GHz"
+    assert bench.host_info(str(tmp_path / "missing"))["cpu_model"]  # falls back to the machine name
+    assert bench.host_info()["nproc"] >= 1
